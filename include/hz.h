@@ -1,0 +1,233 @@
+/*
+ * hz -- GPU domain-decomposition Helmholtz solver (WaveHoltz subdomain solves).
+ *
+ * C ABI of the library libhz.so.  The method is that of "Efficient Domain
+ * Decomposition for the Helmholtz Equation on GPUs" (arXiv 2606.21695):
+ *   - problem: -Lap u - k^2 u = f in Omega, d_n u - i k u = g on dOmega,
+ *     k = omega / c(x), time convention e^{-i omega t}      (Sec. 2, eq. (Helmholtz))
+ *   - discretisation: degree-P GLL spectral elements on a structured quad
+ *     mesh, lumped M and H: (A - i omega H - omega^2 M) u = b
+ *                                                   (Sec. 4, eq. (discrete-helmholtz))
+ *   - non-overlapping subdomains exchanging zeroth-order transmission data
+ *     lambda, updated by lambda_{r,l} = -lambda_{l,r} - 2 i k u_l on the
+ *     interface                                       (Sec. 3, eq. (lambda-iteration);
+ *     the sign of the 2ik term is read as minus, which makes the DD fixed
+ *     point equal to the global discrete solution)
+ *   - each subdomain solved by WaveHoltz (Sec. 5, eq. (WaveHoltz), modified
+ *     leapfrog), one CUDA thread block per subdomain, all subdomains in one
+ *     launch (Sec. 6, Algorithm 1)
+ *   - outer iteration: GMRES on the transmission data (Sec. 3, Krylov
+ *     acceleration) inside FP64 defect correction on the global residual
+ *     (Sec. 7: the DD cycle is a preconditioner and may run in lower precision).
+ *
+ * Conventions for every function below:
+ *   - Return value: HZ_OK or an error code; hz_last_error() gives the message
+ *     of the calling thread's last failure.  No function aborts the process.
+ *   - Handles are owned by the library until the matching *_destroy.
+ *   - Host arrays are owned by the caller and copied on entry / written on exit.
+ *   - Complex arrays are interleaved (re, im) FP64.
+ *   - Node arrays are on the global node grid of (nx*P+1) x (ny*P+1) nodes,
+ *     x index fastest.
+ *   - "device" pointers are CUDA device addresses on the problem's device;
+ *     "stream" is a cudaStream_t (NULL = legacy default stream).  Device
+ *     entry points enqueue work on that stream; they may synchronise it where
+ *     noted.
+ *   - Calls on one problem handle are not thread-safe; server calls are.
+ */
+#ifndef HZ_H
+#define HZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HZ_API __attribute__((visibility("default")))
+#else
+#define HZ_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hz_mesh_s* hz_mesh;
+typedef struct hz_problem_s* hz_problem;
+typedef struct hz_server_s* hz_server;
+
+typedef enum {
+  HZ_OK = 0,
+  HZ_ERR_INVALID_ARG = 1, /* bad size, null pointer, non-finite or non-positive data */
+  HZ_ERR_OOM = 2,         /* device or host allocation failed */
+  HZ_ERR_CUDA = 3,        /* a CUDA call failed (message carries the CUDA error) */
+  HZ_ERR_NOT_CONVERGED = 4, /* tolerance not met within max_sweeps / max_refine */
+  HZ_ERR_DIVERGED = 5,    /* non-finite values (e.g. time step beyond the CFL limit) */
+  HZ_ERR_TIMEOUT = 6,     /* a wait ran out (server poll) */
+  HZ_ERR_BUSY = 7,        /* admission refused: HBM budget or queue full */
+  HZ_ERR_NOT_FOUND = 8,   /* unknown ticket */
+  HZ_ERR_INTERNAL = 9,
+  HZ_ERR_UNSUPPORTED = 10 /* a size or degree outside the compiled kernels */
+} hz_status;
+
+/* Precision of the subdomain WaveHoltz loop (Sec. 7).  The outer GMRES,
+ * refinement and global residual are always FP64. */
+typedef enum { HZ_FP64 = 0, HZ_FP32_REFINE = 1 } hz_precision;
+
+/* Outer iteration on the transmission data (Sec. 3).
+ * GMRES: complex GMRES(m) on (I - S) lambda = g (S: homogeneous sweep).
+ * PLAIN: the fixed-point iteration lambda <- S lambda + g of eq. (lambda-iteration).
+ * RGMRES: real GMRES on the (re, im)-interleaved lambda vector; exact for a
+ *         fixed WaveHoltz count, where the sweep is only real-linear. */
+typedef enum { HZ_OUTER_GMRES = 0, HZ_OUTER_PLAIN = 1, HZ_OUTER_RGMRES = 2 } hz_outer;
+
+typedef enum {
+  HZ_WAVE_SPEED = 0, /* n real values, finite and > 0 (c at every node) */
+  HZ_OMEGA = 1,      /* 1 real value > 0 */
+  HZ_SOURCE = 2,     /* n complex values (f at every node) */
+  HZ_BOUNDARY = 3    /* 2*(nx*P+1) + 2*(ny*P+1) complex values of g on the outer
+                        edges in the order S, E, N, W, each along increasing x
+                        (S, N) or y (E, W); corners carry one value per edge */
+} hz_field;
+
+typedef struct {
+  int32_t precision;     /* hz_precision */
+  double tol;            /* stop when ||b - K u||_2 <= tol ||b||_2 (global, FP64) */
+  int32_t max_sweeps;    /* budget of DD sweeps over the whole solve */
+  int32_t outer;         /* hz_outer */
+  int32_t gmres_restart; /* GMRES restart length m */
+  int32_t wh_iters;      /* WaveHoltz iterations per sweep (maximum if wh_tol > 0) */
+  double wh_tol;         /* > 0: a subdomain stops when ||u^{m+1}-u^m|| <= wh_tol ||u^{m+1}|| */
+  int32_t nt_override;   /* > 0: time steps per period; 0: from the CFL rule */
+  double cfl;            /* dt = cfl * 2 / (c_max sqrt(lx + ly)) */
+  double inner_tol;      /* relative tolerance of each DD solve (GMRES on lambda) */
+  int32_t max_refine;    /* maximum FP64 refinement steps */
+} hz_solve_opts;
+
+typedef struct {
+  int32_t sweeps;        /* DD sweeps (kernel launches of the subdomain solve) */
+  int32_t refinements;   /* FP64 defect-correction steps */
+  int32_t nt;            /* time steps per period used */
+  int32_t wh_iters_max;  /* largest WaveHoltz iteration count of any subdomain */
+  double rel_residual;   /* final ||b - K u|| / ||b|| (FP64, global) */
+  double seconds;        /* wall time of the solve */
+  int64_t dof_updates;   /* sum over sweeps of subdomain nodes x (N_t - 1) x WaveHoltz iterations */
+  int32_t gmres_iters;   /* total GMRES iterations */
+  int32_t reserved;
+  double sweep_seconds;  /* device time of the sweep kernels (CUDA events on the solve's stream) */
+} hz_solve_report;
+
+/* Defaults: FP64, tol 1e-8, 2000 sweeps, GMRES(60), 10 WaveHoltz iterations,
+ * no wh_tol, CFL 0.9, inner_tol 1e-6, 20 refinements. */
+HZ_API void hz_default_opts(hz_solve_opts* opts);
+
+/* Copies the calling thread's last error message (NUL-terminated, truncated
+ * to n bytes).  Returns HZ_OK. */
+HZ_API hz_status hz_last_error(char* buf, size_t n);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all devices, all threads).  Not part of the method; for accounting. */
+HZ_API hz_status hz_kernel_launches(uint64_t* count);
+
+/* ------------------------------------------------------------------ mesh --
+ * Structured mesh of [x0,x1] x [y0,y1] with nx x ny quad elements of degree
+ * P (1..7), split into subdomains of sub_nx x sub_ny elements (Sec. 3, Fig. 1;
+ * Sec. 4).  sub_nx must divide nx and sub_ny divide ny.  Errors:
+ * HZ_ERR_INVALID_ARG on bad sizes or an empty box. */
+HZ_API hz_status hz_mesh_create(double x0, double x1, double y0, double y1, int32_t nx, int32_t ny, int32_t degree,
+                         int32_t sub_nx, int32_t sub_ny, hz_mesh* out);
+/* n = (nx*P+1)*(ny*P+1). */
+HZ_API hz_status hz_mesh_num_nodes(hz_mesh mesh, int64_t* n);
+/* Writes the 2n node coordinates (x, y) interleaved, x index fastest, into the
+ * caller's buffer xy (GLL node positions, Sec. 4). */
+HZ_API hz_status hz_mesh_node_coords(hz_mesh mesh, double* xy);
+HZ_API void hz_mesh_destroy(hz_mesh mesh);
+
+/* --------------------------------------------------------------- problem --
+ * A problem on a mesh, resident on CUDA device `device`.  The problem keeps a
+ * reference to the mesh (the mesh may be destroyed by the caller afterwards). */
+HZ_API hz_status hz_problem_create(hz_mesh mesh, int32_t device, hz_problem* out);
+/* Copies a field from host memory (count values as described by hz_field;
+ * complex fields count complex numbers).  Validates finiteness and c > 0. */
+HZ_API hz_status hz_problem_set(hz_problem pr, hz_field field, const double* data, int64_t count);
+/* Same from device memory (copied device-to-device on `stream`, which is
+ * synchronised). */
+HZ_API hz_status hz_problem_set_device(hz_problem pr, hz_field field, const double* data, int64_t count, void* stream);
+HZ_API void hz_problem_destroy(hz_problem pr);
+
+/* Time steps per period from the CFL rule: N_t = max(3, ceil((2 pi/omega)/dt))
+ * with dt = cfl * 2 / (c_max sqrt(lx + ly)), lx, ly the largest eigenvalues
+ * of the 1D subdomain stiffness over its lumped mass (Sec. 5; the paper's
+ * dt <= 2h/(p^2 c_max) is replaced by this exact bound). */
+HZ_API hz_status hz_problem_nt(hz_problem pr, double cfl, int32_t* nt);
+
+/* ------------------------------------------------------------------ solve --
+ * Full solve to opts->tol: FP64 defect correction u <- u + DD(b - K u), each
+ * DD step an outer iteration on lambda whose matvec is one sweep (one kernel
+ * launch over all subdomains).  u_out: host buffer of n complex values.
+ * Returns HZ_ERR_NOT_CONVERGED (report filled, u_out written) if the budget
+ * runs out, HZ_ERR_DIVERGED on non-finite values. */
+HZ_API hz_status hz_solve(hz_problem pr, const hz_solve_opts* opts, double* u_out, hz_solve_report* report);
+/* Same with the solution written to device memory u_out_dev (n complex). */
+HZ_API hz_status hz_solve_device(hz_problem pr, const hz_solve_opts* opts, double* u_out_dev, hz_solve_report* report,
+                          void* stream);
+
+/* ------------------------------------------------- hot-path step calls --
+ * These expose the individual steps of the path on device buffers.
+ *
+ * Transmission data layout ("lambda vector"): L*4*NE complex values,
+ * L = number of subdomains (x index fastest), 4 edges per subdomain in the
+ * order W, E, S, N, NE = max(sub_nx, sub_ny)*P + 1 nodes per edge along
+ * increasing x (S, N) or y (W, E); unused tail entries and the slots of
+ * edges on the outer boundary are zero on output. */
+HZ_API hz_status hz_lambda_size(hz_problem pr, int64_t* n_complex);
+
+/* Prepares the per-subdomain leapfrog coefficients (alpha, beta of Sec. 5)
+ * for nt time steps per period.  Called implicitly by the functions below
+ * when nt changes. */
+HZ_API hz_status hz_prepare(hz_problem pr, int32_t nt, void* stream);
+
+/* One DD sweep (Algorithm 1 on every subdomain, one thread block each, one
+ * launch): assemble b from the split global source rhs (NULL = homogeneous)
+ * and lam_in, run wh_iters WaveHoltz iterations (wh_tol as in
+ * hz_solve_opts), write lam_out (lambda vector) and, if u_sub is not NULL,
+ * the subdomain solutions (L x nly x nlx complex, nly = sub_ny*P+1,
+ * nlx = sub_nx*P+1, subdomain-major).  precision: hz_precision of the loop. */
+HZ_API hz_status hz_sweep(hz_problem pr, int32_t precision, int32_t nt, int32_t wh_iters, double wh_tol,
+                   const double* lam_in, double* lam_out, const double* rhs, double* u_sub, void* stream);
+
+/* Global weak-form right-hand side b = (f, phi) + <g, phi> (Sec. 4), n complex. */
+HZ_API hz_status hz_rhs(hz_problem pr, double* b, void* stream);
+
+/* r = b - (A - i omega H - omega^2 M) u on the whole mesh, FP64, n complex
+ * (Sec. 4, matrix-free).  If norms2 is not NULL it receives ||r||^2 and
+ * ||b||^2 (2 doubles, device memory).  b may be NULL (treated as zero, so
+ * r = -K u).  Uses library-owned scratch for the reduction. */
+HZ_API hz_status hz_residual(hz_problem pr, const double* b, const double* u, double* r, double* norms2, void* stream);
+
+/* u += mass-weighted average of the subdomain copies u_sub (the inverse of the
+ * splitting of a global right-hand side by lumped-mass share). */
+HZ_API hz_status hz_assemble_add(hz_problem pr, const double* u_sub, double* u, void* stream);
+
+/* ------------------------------------------------------------------ server --
+ * Continuous-batching request server on one device: submitted solves are
+ * admitted against an HBM budget and advanced together, one sweep of every
+ * active solve per scheduling tick. */
+HZ_API hz_status hz_server_create(int32_t device, uint64_t hbm_budget_bytes, hz_server* out);
+/* Snapshots the problem (fields are copied) and queues a solve. */
+HZ_API hz_status hz_server_submit(hz_server srv, hz_problem pr, const hz_solve_opts* opts, uint64_t* ticket);
+/* timeout_ms < 0 waits without limit, 0 polls.  On completion writes u_out
+ * (host, n complex; may be NULL) and the report, sets *done = 1 and forgets
+ * the ticket; otherwise *done = 0 and HZ_ERR_TIMEOUT after a positive
+ * timeout.  The solve's own status is returned when done. */
+HZ_API hz_status hz_server_poll(hz_server srv, uint64_t ticket, int32_t timeout_ms, double* u_out, hz_solve_report* report,
+                         int32_t* done);
+/* Latency percentiles (submit to completion) over completed requests,
+ * completed solves per second since creation, device bytes held now. */
+HZ_API hz_status hz_server_stats(hz_server srv, double* p50_ms, double* p99_ms, double* solves_per_s, uint64_t* hbm_in_use);
+/* Cancels queued requests, finishes or abandons in-flight ones, frees all. */
+HZ_API void hz_server_destroy(hz_server srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HZ_H */

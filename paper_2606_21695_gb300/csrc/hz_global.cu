@@ -1,0 +1,377 @@
+// FP64 kernels around the sweep: leapfrog coefficients, right-hand side,
+// global operator residual, assembly of subdomain copies, and the vector
+// operations of the outer Krylov iteration.  All are HBM-bound streaming
+// kernels with coalesced x-fastest access; reductions are two-pass with a
+// fixed summation order (deterministic results).
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "hz_internal.h"
+
+namespace hz {
+namespace {
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of NV values per thread into out[0..NV-1] (thread 0 holds result).
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double* out) {
+  __shared__ double sh[NV][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = warp_sum(v[k]);
+    if (lane == 0) sh[k][warp] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double x = (lane < nw) ? sh[k][lane] : 0.0;
+      x = warp_sum(x);
+      if (lane == 0) out[k] = x;
+    }
+  }
+}
+
+// ---- leapfrog coefficients (Sec. 5): per subdomain node
+//   M = Wx_i Wy_j / c^2, H = (edge weights over all four subdomain edges) / c
+//   alpha = (M - theta H)/(M + theta H), beta = sigma/(M + theta H)
+__global__ void prepare_kernel(const __grid_constant__ PrepArgs a) {
+  const int l = blockIdx.y;
+  const int nn = a.nlx * a.nly;
+  const int sxi = l % a.Sx, syi = l / a.Sx;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < nn; n += gridDim.x * blockDim.x) {
+    const int i = n % a.nlx, j = n / a.nlx;
+    const int64_t I = (int64_t)sxi * a.snxP + i, J = (int64_t)syi * a.snyP + j;
+    const double c = a.c[J * a.NXg + I];
+    const double M = a.wxs[i] * a.wys[j] / (c * c);
+    const double Hw = ((j == 0 || j == a.nly - 1) ? a.wxs[i] : 0.0) + ((i == 0 || i == a.nlx - 1) ? a.wys[j] : 0.0);
+    const double H = Hw / c;
+    const double den = M + a.theta * H;
+    const double be = a.sigma / den;
+    const double al = (M - a.theta * H) / den;
+    const int64_t k = (int64_t)l * nn + n;
+    a.beta64[k] = be;
+    a.alpha64[k] = al;
+    a.beta32[k] = (float)be;
+    a.alpha32[k] = (float)al;
+  }
+  if (blockIdx.x == 0) {
+    for (int k = threadIdx.x; k < 4 * a.NE; k += blockDim.x) {
+      const int e = k / a.NE, t = k % a.NE;
+      const int len = (e < 2) ? a.nly : a.nlx;
+      double val = 0.0;
+      if (t < len) {
+        const int i = (e == 0) ? 0 : (e == 1) ? a.nlx - 1 : t;
+        const int j = (e == 2) ? 0 : (e == 3) ? a.nly - 1 : t;
+        const int64_t I = (int64_t)sxi * a.snxP + i, J = (int64_t)syi * a.snyP + j;
+        val = a.omega / a.c[J * a.NXg + I];
+      }
+      a.kedge[(int64_t)l * 4 * a.NE + k] = val;
+    }
+  }
+}
+
+// ---- b = (f, phi) + <g, phi>, lumped GLL quadrature (Sec. 4)
+__global__ void rhs_kernel(const __grid_constant__ GlobalArgs a, const double* __restrict__ f,
+                           const double* __restrict__ gb, double* __restrict__ b) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y;
+  if (I >= a.NXg) return;
+  const int64_t n = (int64_t)J * a.NXg + I;
+  const double wx = a.Wxg[I], wy = a.Wyg[J];
+  double br = wx * wy * f[2 * n], bi = wx * wy * f[2 * n + 1];
+  const int64_t oS = 0, oE = a.NXg, oN = a.NXg + a.NYg, oW = 2 * a.NXg + a.NYg;
+  if (J == 0) { br += wx * gb[2 * (oS + I)]; bi += wx * gb[2 * (oS + I) + 1]; }
+  if (J == a.NYg - 1) { br += wx * gb[2 * (oN + I)]; bi += wx * gb[2 * (oN + I) + 1]; }
+  if (I == 0) { br += wy * gb[2 * (oW + J)]; bi += wy * gb[2 * (oW + J) + 1]; }
+  if (I == a.NXg - 1) { br += wy * gb[2 * (oE + J)]; bi += wy * gb[2 * (oE + J) + 1]; }
+  b[2 * n] = br;
+  b[2 * n + 1] = bi;
+}
+
+// ---- r = b - (A - i w H - w^2 M) u on the global grid (Sec. 4), FP64.
+// A u = Wy_J (Kx u)_IJ + Wx_I (Ky u)_IJ with assembled 1D rows built from the
+// reference element stiffness (one-sided at the outer boundary).
+template <int P>
+__global__ void residual_kernel(const __grid_constant__ GlobalArgs a, const double* __restrict__ b,
+                                const double* __restrict__ u, double* __restrict__ r, double* __restrict__ part) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  double sums[2] = {0.0, 0.0};
+  if (I < a.NXg && J < a.NYg) {
+    const int64_t n = (int64_t)J * a.NXg + I;
+    const double2* u2 = reinterpret_cast<const double2*>(u);
+    // x row
+    const int ax = I % P, ex = I / P;
+    const bool own_x = ex < a.nx, left_x = (ax == 0) && ex >= 1;
+    double sxr = 0.0, sxi = 0.0;
+#pragma unroll
+    for (int tt = -P; tt <= P; ++tt) {
+      double cf = 0.0;
+      const int bb = ax + tt;
+      const bool in_own = own_x && bb >= 0 && bb <= P, in_left = left_x && tt <= 0;
+      if (in_own) cf += a.Kref[ax * (P + 1) + bb];
+      if (in_left) cf += a.Kref[P * (P + 1) + (tt + P)];
+      if (in_own || in_left) {  // structurally inside the mesh
+        const double2 v = __ldg(&u2[n + tt]);
+        sxr += cf * v.x;
+        sxi += cf * v.y;
+      }
+    }
+    const int ay = J % P, ey = J / P;
+    const bool own_y = ey < a.ny, below_y = (ay == 0) && ey >= 1;
+    double syr = 0.0, syi = 0.0;
+#pragma unroll
+    for (int tt = -P; tt <= P; ++tt) {
+      double cf = 0.0;
+      const int bb = ay + tt;
+      const bool in_own = own_y && bb >= 0 && bb <= P, in_below = below_y && tt <= 0;
+      if (in_own) cf += a.Kref[ay * (P + 1) + bb];
+      if (in_below) cf += a.Kref[P * (P + 1) + (tt + P)];
+      if (in_own || in_below) {
+        const double2 v = __ldg(&u2[n + (int64_t)tt * a.NXg]);
+        syr += cf * v.x;
+        syi += cf * v.y;
+      }
+    }
+    const double Wx = a.Wxg[I], Wy = a.Wyg[J];
+    const double Aur = Wy * a.kxs * sxr + Wx * a.kys * syr;
+    const double Aui = Wy * a.kxs * sxi + Wx * a.kys * syi;
+    const double c = a.c[n];
+    const double M = Wx * Wy / (c * c);
+    const double H = (((J == 0 || J == a.NYg - 1) ? Wx : 0.0) + ((I == 0 || I == a.NXg - 1) ? Wy : 0.0)) / c;
+    const double2 un = u2[n];
+    const double w = a.omega;
+    // K u = A u - i w H u - w^2 M u
+    const double Kur = Aur + w * H * un.y - w * w * M * un.x;
+    const double Kui = Aui - w * H * un.x - w * w * M * un.y;
+    double br = 0.0, bi = 0.0;
+    if (b) { br = b[2 * n]; bi = b[2 * n + 1]; }
+    const double rr = br - Kur, ri = bi - Kui;
+    r[2 * n] = rr;
+    r[2 * n + 1] = ri;
+    sums[0] = rr * rr + ri * ri;
+    sums[1] = br * br + bi * bi;
+  }
+  // flatten the 2D block for the reduction
+  __shared__ double out[2];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  {
+    __shared__ double sh[2][32];
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    for (int k = 0; k < 2; ++k) {
+      double x = warp_sum(sums[k]);
+      if (lane == 0) sh[k][warp] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int k = 0; k < 2; ++k) {
+        double x = (lane < nw) ? sh[k][lane] : 0.0;
+        x = warp_sum(x);
+        if (lane == 0) out[k] = x;
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+    part[2 * blk] = out[0];
+    part[2 * blk + 1] = out[1];
+  }
+}
+
+// out[k] = sum_blk part[blk * width + k], fixed order; one block per k.
+__global__ void reduce_partials_kernel(const double* __restrict__ part, int nblocks, int width,
+                                       double* __restrict__ out) {
+  const int k = blockIdx.x;
+  double v[1] = {0.0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v[0] += part[(int64_t)b * width + k];
+  __shared__ double res[1];
+  block_sum<1>(v, res);
+  if (threadIdx.x == 0) out[k] = res[0];
+}
+
+// u += average of the subdomain copies at every global node (share 1/count
+// per copy: 1, 1/2 on interfaces, 1/4 at cross points; uniform mesh).
+__global__ void assemble_add_kernel(const __grid_constant__ AssembleArgs a, const double* __restrict__ u_sub,
+                                    double* __restrict__ u) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y;
+  if (I >= a.NXg) return;
+  int sx1 = I / a.snxP, sx0 = sx1;
+  if (sx1 >= a.Sx) { sx1 = a.Sx - 1; sx0 = sx1; }
+  else if (I % a.snxP == 0 && I > 0) sx0 = sx1 - 1;
+  int sy1 = J / a.snyP, sy0 = sy1;
+  if (sy1 >= a.Sy) { sy1 = a.Sy - 1; sy0 = sy1; }
+  else if (J % a.snyP == 0 && J > 0) sy0 = sy1 - 1;
+  const double share = 1.0 / (double)((sx1 - sx0 + 1) * (sy1 - sy0 + 1));
+  const int64_t nn = (int64_t)a.nlx * a.nly;
+  double sr = 0.0, si = 0.0;
+  for (int sy = sy0; sy <= sy1; ++sy)
+    for (int sx = sx0; sx <= sx1; ++sx) {
+      const int l = sy * a.Sx + sx;
+      const int i = I - sx * a.snxP, j = J - sy * a.snyP;
+      const int64_t k = (int64_t)l * nn + (int64_t)j * a.nlx + i;
+      sr += u_sub[2 * k];
+      si += u_sub[2 * k + 1];
+    }
+  const int64_t n = (int64_t)J * a.NXg + I;
+  u[2 * n] += share * sr;
+  u[2 * n + 1] += share * si;
+}
+
+// ---- Krylov vector kernels (vectors of n2 doubles = n2/2 complex values)
+__global__ void multi_dot_kernel(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ w,
+                                 int64_t n2, int real_dot, double* __restrict__ part) {
+  const int k = blockIdx.y;
+  const double* v = V + (int64_t)k * ld;
+  double s[2] = {0.0, 0.0};
+  const int64_t nc = n2 / 2;
+  const double2* v2 = reinterpret_cast<const double2*>(v);
+  const double2* w2 = reinterpret_cast<const double2*>(w);
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += (int64_t)gridDim.x * blockDim.x) {
+    const double2 a = v2[q], b = w2[q];
+    s[0] += a.x * b.x + a.y * b.y;  // Re conj(a) b  (= real dot of the pair)
+    if (!real_dot) s[1] += a.x * b.y - a.y * b.x;  // Im conj(a) b
+  }
+  __shared__ double out[2];
+  block_sum<2>(s, out);
+  if (threadIdx.x == 0) {
+    double* p = part + ((int64_t)blockIdx.x * nv + k) * 2;
+    p[0] = out[0];
+    p[1] = out[1];
+  }
+}
+
+__global__ void multi_axpy_kernel(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ h,
+                                  double* __restrict__ w, int64_t n2, int real_coef) {
+  extern __shared__ double hs[];
+  for (int k = threadIdx.x; k < 2 * nv; k += blockDim.x) hs[k] = h[k];
+  __syncthreads();
+  const int64_t nc = n2 / 2;
+  double2* w2 = reinterpret_cast<double2*>(w);
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += (int64_t)gridDim.x * blockDim.x) {
+    double2 acc = w2[q];
+    for (int k = 0; k < nv; ++k) {
+      const double2 v = reinterpret_cast<const double2*>(V + (int64_t)k * ld)[q];
+      const double hr = hs[2 * k], hi = real_coef ? 0.0 : hs[2 * k + 1];
+      acc.x -= hr * v.x - hi * v.y;
+      acc.y -= hr * v.y + hi * v.x;
+    }
+    w2[q] = acc;
+  }
+}
+
+__global__ void axpby_kernel(double a, const double* __restrict__ x, double b, double* __restrict__ y, int64_t n2) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n2; q += (int64_t)gridDim.x * blockDim.x)
+    y[q] = a * x[q] + b * y[q];
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g > 152 * 8) g = 152 * 8;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <int P>
+hz_status launch_residual_P(const GlobalArgs& a, const double* b, const double* u, double* r, double* part,
+                            int* nb, cudaStream_t st) {
+  dim3 blk(32, 8);
+  dim3 grd((a.NXg + 31) / 32, (a.NYg + 7) / 8);
+  residual_kernel<P><<<grd, blk, 0, st>>>(a, b, u, r, part);
+  note_launch();
+  HZ_CUDA(cudaGetLastError());
+  *nb = (int)(grd.x * grd.y);
+  return HZ_OK;
+}
+
+}  // namespace
+
+hz_status launch_prepare(const PrepArgs& a, int L, cudaStream_t st) {
+  const int nn = a.nlx * a.nly;
+  dim3 grd((nn + 255) / 256, L);
+  prepare_kernel<<<grd, 256, 0, st>>>(a);
+  note_launch();
+  HZ_CUDA(cudaGetLastError());
+  return HZ_OK;
+}
+
+hz_status launch_rhs(const GlobalArgs& a, const double* f, const double* gb, double* b, cudaStream_t st) {
+  dim3 grd((a.NXg + 127) / 128, a.NYg);
+  rhs_kernel<<<grd, 128, 0, st>>>(a, f, gb, b);
+  note_launch();
+  HZ_CUDA(cudaGetLastError());
+  return HZ_OK;
+}
+
+int residual_blocks(const GlobalArgs& a) { return ((a.NXg + 31) / 32) * ((a.NYg + 7) / 8); }
+
+hz_status launch_residual(const GlobalArgs& a, const double* b, const double* u, double* r, double* part,
+                          int* nblocks, cudaStream_t st) {
+  switch (a.P) {
+    case 1: return launch_residual_P<1>(a, b, u, r, part, nblocks, st);
+    case 2: return launch_residual_P<2>(a, b, u, r, part, nblocks, st);
+    case 3: return launch_residual_P<3>(a, b, u, r, part, nblocks, st);
+    case 4: return launch_residual_P<4>(a, b, u, r, part, nblocks, st);
+    case 5: return launch_residual_P<5>(a, b, u, r, part, nblocks, st);
+    case 6: return launch_residual_P<6>(a, b, u, r, part, nblocks, st);
+    case 7: return launch_residual_P<7>(a, b, u, r, part, nblocks, st);
+    default: return fail(HZ_ERR_UNSUPPORTED, "degree outside 1..7");
+  }
+}
+
+hz_status launch_reduce_partials(const double* part, int nblocks, int width, double* out, cudaStream_t st) {
+  reduce_partials_kernel<<<width, kRedThreads, 0, st>>>(part, nblocks, width, out);
+  note_launch();
+  HZ_CUDA(cudaGetLastError());
+  return HZ_OK;
+}
+
+hz_status launch_assemble_add(const AssembleArgs& a, const double* u_sub, double* u, cudaStream_t st) {
+  dim3 grd((a.NXg + 127) / 128, a.NYg);
+  assemble_add_kernel<<<grd, 128, 0, st>>>(a, u_sub, u);
+  note_launch();
+  HZ_CUDA(cudaGetLastError());
+  return HZ_OK;
+}
+
+int vec_blocks(int64_t n2) { return grid_for(n2 / 2, kRedThreads) > 304 ? 304 : grid_for(n2 / 2, kRedThreads); }
+
+hz_status launch_multi_dot(const double* V, int64_t ld, int nv, const double* w, int64_t n2, bool real_dot,
+                           double* part, int nblocks, cudaStream_t st) {
+  dim3 grd(nblocks, nv);
+  multi_dot_kernel<<<grd, kRedThreads, 0, st>>>(V, ld, nv, w, n2, real_dot ? 1 : 0, part);
+  note_launch();
+  HZ_CUDA(cudaGetLastError());
+  return HZ_OK;
+}
+
+hz_status launch_multi_axpy(const double* V, int64_t ld, int nv, const double* h, double* w, int64_t n2,
+                            bool real_coef, cudaStream_t st) {
+  const int g = grid_for(n2 / 2, 256);
+  multi_axpy_kernel<<<g, 256, (size_t)2 * nv * sizeof(double), st>>>(V, ld, nv, h, w, n2, real_coef ? 1 : 0);
+  note_launch();
+  HZ_CUDA(cudaGetLastError());
+  return HZ_OK;
+}
+
+hz_status launch_axpby(double a, const double* x, double b, double* y, int64_t n2, cudaStream_t st) {
+  axpby_kernel<<<grid_for(n2, 256), 256, 0, st>>>(a, x, b, y, n2);
+  note_launch();
+  HZ_CUDA(cudaGetLastError());
+  return HZ_OK;
+}
+
+}  // namespace hz

@@ -1,0 +1,159 @@
+// Internal declarations shared by the host runtime (.cpp) and the kernels (.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hz.h"
+
+namespace hz {
+
+constexpr int kMaxP = 7;
+
+// ------------------------------------------------------------- errors ----
+void set_error(const std::string& msg);
+hz_status fail(hz_status s, const std::string& msg);
+hz_status cuda_fail(cudaError_t e, const char* what);
+void note_launch();  // counts kernel launches (hz_kernel_launches)
+
+#define HZ_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return ::hz::cuda_fail(e_, #call); \
+  } while (0)
+
+#define HZ_TRY(call)                     \
+  do {                                   \
+    hz_status s_ = (call);               \
+    if (s_ != HZ_OK) return s_;          \
+  } while (0)
+
+// ------------------------------------------------------- device memory ----
+// Owning device buffer (cudaMalloc on the problem's device).
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  hz_status ensure(size_t nbytes);  // grows (contents not kept)
+  void release();
+  template <typename T>
+  T* as() const { return static_cast<T*>(ptr); }
+};
+
+// --------------------------------------------------------- mesh geometry ----
+struct Geom {
+  double x0, x1, y0, y1, hx, hy;
+  int nx, ny, P, snx, sny;
+  int Sx, Sy, L;          // subdomain grid
+  int NXg, NYg;           // global nodes per direction
+  int nlx, nly, NE;       // subdomain nodes per direction, lambda slot length
+  int64_t n;              // global nodes
+  std::vector<double> xi, w;        // GLL nodes / weights on [-1, 1]
+  std::vector<double> Kref;         // (P+1)^2: integral of l_a' l_b' over [-1,1], row a
+  std::vector<double> Wxg, Wyg;     // global lumped 1D weights
+  std::vector<double> Wxs, Wys;     // subdomain lumped 1D weights
+  int64_t sub_nodes() const { return (int64_t)nlx * nly; }
+  int64_t lam_complex() const { return (int64_t)L * 4 * NE; }
+};
+
+hz_status build_geom(double x0, double x1, double y0, double y1, int nx, int ny, int P, int snx, int sny, Geom* g);
+double max_eig_1d(const Geom& g, int n_el, double h);  // largest eig of W^-1 K, 1D subdomain
+
+// ------------------------------------------------------------- kernels ----
+struct SweepArgs {
+  int nlx, nly, NE, Sx, Sy, sxe, sye, NXg, NS, snxP, snyP;
+  int Nt, m_wh;
+  double wh_tol, sigma, omega, cpi, spi, two_over_nt;
+  double kxs, kys, hx2, hy2;  // 2/hx, 2/hy, hx/2, hy/2
+  double Kref[(kMaxP + 1) * (kMaxP + 1)];
+  float Kref32[(kMaxP + 1) * (kMaxP + 1)];
+  double w[kMaxP + 1];
+  const void* beta;   // [L][nly][nlx] Real
+  const void* alpha;  // [L][nly][nlx] Real
+  const void* tab;    // [Nt+1] x 4 Real: cos(2 pi nu/Nt), sin(2 pi nu/Nt), kappa_nu, kappa_{nu+1/2}/omega
+  const double* kedge;  // [L][4][NE] omega / c at edge nodes
+  const double* wxs;    // [nlx]
+  const double* wys;    // [nly]
+  const double* rhs;    // global complex or null
+  const double* lam_in;
+  double* lam_out;
+  double* u_sub;        // [L][nly][nlx] complex or null
+  int* wh_iter_max;
+  unsigned long long* wh_iter_sum;  // sum over subdomains of WaveHoltz iterations
+  int* flags;           // bit 0: non-finite value seen
+};
+
+// Launches the sweep in Real = float (fp32 = true) or double.  Returns
+// HZ_ERR_UNSUPPORTED when no compiled variant fits the subdomain.
+hz_status launch_sweep_f32(int P, const SweepArgs& a, int L, cudaStream_t st);
+hz_status launch_sweep_f64(int P, const SweepArgs& a, int L, cudaStream_t st);
+inline hz_status launch_sweep(bool fp32, int P, const SweepArgs& a, int L, cudaStream_t st) {
+  return fp32 ? launch_sweep_f32(P, a, L, st) : launch_sweep_f64(P, a, L, st);
+}
+
+struct PrepArgs {
+  int nlx, nly, NE, Sx, Sy, NXg, snxP, snyP;
+  double theta, sigma, omega;
+  const double* c;      // global
+  const double* wxs;
+  const double* wys;
+  double* beta64;
+  double* alpha64;
+  float* beta32;
+  float* alpha32;
+  double* kedge;
+};
+hz_status launch_prepare(const PrepArgs& a, int L, cudaStream_t st);
+
+struct GlobalArgs {
+  int NXg, NYg, nx, ny, P;
+  double omega, kxs, kys, hx2, hy2;
+  double Kref[(kMaxP + 1) * (kMaxP + 1)];
+  double w[kMaxP + 1];
+  const double* c;
+  const double* Wxg;
+  const double* Wyg;
+};
+// b = (f, phi) + <g, phi>; f: n complex; gb: boundary S,E,N,W complex.
+hz_status launch_rhs(const GlobalArgs& a, const double* f, const double* gb, double* b, cudaStream_t st);
+// r = b - K u (b may be null); partial sums of |r|^2, |b|^2 per block into part (2 per block);
+// returns the number of blocks used through *nblocks.
+hz_status launch_residual(const GlobalArgs& a, const double* b, const double* u, double* r, double* part,
+                          int* nblocks, cudaStream_t st);
+int residual_blocks(const GlobalArgs& a);
+// out[k] = sum over blocks of part[blocks][k] for k < width, in fixed order.
+hz_status launch_reduce_partials(const double* part, int nblocks, int width, double* out, cudaStream_t st);
+
+struct AssembleArgs {
+  int nlx, nly, Sx, Sy, NXg, NYg, snxP, snyP;
+};
+hz_status launch_assemble_add(const AssembleArgs& a, const double* u_sub, double* u, cudaStream_t st);
+
+// ---- FP64 vector kernels for the outer Krylov iteration (complex, interleaved)
+// part[blk][2k..2k+1] = partial sum over this block of conj(V_k) . w (complex) or
+// real dot (real_dot = true, imaginary part 0), k = 0..nv-1; V_k = V + k*ld.
+int vec_blocks(int64_t n2);
+hz_status launch_multi_dot(const double* V, int64_t ld, int nv, const double* w, int64_t n2, bool real_dot,
+                           double* part, int nblocks, cudaStream_t st);
+// w -= sum_k h[k] V_k  (h complex on device, nv entries)
+hz_status launch_multi_axpy(const double* V, int64_t ld, int nv, const double* h, double* w, int64_t n2,
+                            bool real_coef, cudaStream_t st);
+// y = alpha * x (alpha real, on device at *alpha_inv as 1/alpha); y may alias x
+hz_status launch_scale(const double* x, const double* norm, double* y, int64_t n2, cudaStream_t st);
+// y = x (copy)
+hz_status launch_copy(const double* x, double* y, int64_t n2, cudaStream_t st);
+// y = x - y  (for r = g - (I - S) lam: helper)   y = a*x + b*y
+hz_status launch_axpby(double a, const double* x, double b, double* y, int64_t n2, cudaStream_t st);
+
+}  // namespace hz
+
+// Library-side objects behind the opaque handles.
+struct hz_mesh_s {
+  hz::Geom g;
+};

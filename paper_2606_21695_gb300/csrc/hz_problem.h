@@ -1,0 +1,58 @@
+// Problem state behind the opaque hz_problem handle.
+#pragma once
+
+#include <vector>
+
+#include "hz_internal.h"
+
+namespace hz {
+
+// Owning pinned host buffer (for the small device-to-host reads of the outer loop).
+struct HostBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  HostBuf() = default;
+  HostBuf(const HostBuf&) = delete;
+  HostBuf& operator=(const HostBuf&) = delete;
+  ~HostBuf();
+  hz_status ensure(size_t nbytes);
+};
+
+}  // namespace hz
+
+struct hz_problem_s {
+  hz::Geom g;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  double omega = 0.0, cmax = 0.0, sigma = 0.0;
+  bool has_c = false, has_omega = false;
+  int version = 0;            // bumped on every field change
+  int prepared_nt = 0, prepared_version = -1;
+  long long sweeps_launched = 0;
+  // fields (global node grid)
+  hz::DevBuf c, f, gb;
+  // 1D weight tables
+  hz::DevBuf Wxg, Wyg, wxs, wys;
+  // leapfrog coefficients for prepared_nt
+  hz::DevBuf beta64, alpha64, beta32, alpha32, kedge, tab64, tab32;
+  // solver workspace
+  hz::DevBuf bvec, rvec, uvec, usub, gv, xv, tv, V, part, small, flags;
+  hz::HostBuf hsmall;
+  // per-sweep CUDA events while a solve runs (report.sweep_seconds)
+  bool time_sweeps = false;
+  size_t ev_used = 0;
+  std::vector<cudaEvent_t> events;
+};
+
+namespace hz {
+using Problem = hz_problem_s;
+int choose_nt(const Problem& pr, double cfl);
+hz_status prepare(Problem& pr, int nt, cudaStream_t st);
+hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, const double* lam_in, double* lam_out,
+                const double* rhs, double* u_sub, cudaStream_t st);
+hz_status residual(Problem& pr, const double* b, const double* u, double* r, double* norms2_dev, cudaStream_t st);
+hz_status rhs(Problem& pr, double* b, cudaStream_t st);
+hz_status assemble_add(Problem& pr, const double* u_sub, double* u, cudaStream_t st);
+hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report* rep, cudaStream_t st);
+hz_status check_ready(const Problem& pr);
+}  // namespace hz

@@ -1,0 +1,872 @@
+// Host runtime behind the C ABI: problem state, coefficient preparation,
+// the outer iteration on the transmission data (GMRES / plain / real GMRES,
+// Sec. 3), FP64 defect correction on the global residual (Sec. 7), and the
+// extern "C" entry points declared in include/hz.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "hz_internal.h"
+#include "hz_problem.h"
+
+namespace hz {
+
+// ------------------------------------------------------------- errors ----
+namespace {
+thread_local std::string g_last_error;
+std::atomic<unsigned long long> g_launches{0};
+}
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void set_error(const std::string& msg) { g_last_error = msg; }
+hz_status fail(hz_status s, const std::string& msg) {
+  set_error(msg);
+  return s;
+}
+hz_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(HZ_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+hz_status DevBuf::ensure(size_t nbytes) {
+  if (nbytes <= bytes && ptr) return HZ_OK;
+  release();
+  if (nbytes == 0) nbytes = 16;
+  cudaError_t e = cudaMalloc(&ptr, nbytes);
+  if (e != cudaSuccess) {
+    ptr = nullptr;
+    bytes = 0;
+    (void)cudaGetLastError();
+    return fail(HZ_ERR_OOM, std::string("device allocation of ") + std::to_string(nbytes) + " bytes failed: " +
+                                cudaGetErrorString(e));
+  }
+  bytes = nbytes;
+  return HZ_OK;
+}
+void DevBuf::release() {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  bytes = 0;
+}
+
+HostBuf::~HostBuf() {
+  if (ptr) cudaFreeHost(ptr);
+}
+hz_status HostBuf::ensure(size_t nbytes) {
+  if (nbytes <= bytes && ptr) return HZ_OK;
+  if (ptr) cudaFreeHost(ptr);
+  ptr = nullptr;
+  bytes = 0;
+  if (cudaHostAlloc(&ptr, nbytes, cudaHostAllocDefault) != cudaSuccess) {
+    ptr = nullptr;
+    (void)cudaGetLastError();
+    return fail(HZ_ERR_OOM, "pinned host allocation failed");
+  }
+  bytes = nbytes;
+  return HZ_OK;
+}
+
+// ---------------------------------------------------------- problem ops ----
+int choose_nt(const Problem& pr, double cfl) {
+  const Geom& g = pr.g;
+  const double lx = max_eig_1d(g, g.snx, g.hx);
+  const double ly = max_eig_1d(g, g.sny, g.hy);
+  const double lam = pr.cmax * pr.cmax * (lx + ly);
+  const double dt_max = cfl * 2.0 / std::sqrt(lam);
+  const double T = 2.0 * M_PI / pr.omega;
+  const double q = std::ceil(T / dt_max);
+  return std::max(3, (int)q);
+}
+
+static GlobalArgs global_args(const Problem& pr) {
+  const Geom& g = pr.g;
+  GlobalArgs a{};
+  a.NXg = g.NXg;
+  a.NYg = g.NYg;
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.P = g.P;
+  a.omega = pr.omega;
+  a.kxs = 2.0 / g.hx;
+  a.kys = 2.0 / g.hy;
+  a.hx2 = g.hx / 2.0;
+  a.hy2 = g.hy / 2.0;
+  for (size_t k = 0; k < g.Kref.size(); ++k) a.Kref[k] = g.Kref[k];
+  for (int k = 0; k <= g.P; ++k) a.w[k] = g.w[k];
+  a.c = pr.c.as<double>();
+  a.Wxg = pr.Wxg.as<double>();
+  a.Wyg = pr.Wyg.as<double>();
+  return a;
+}
+
+hz_status check_ready(const Problem& pr) {
+  if (!pr.has_c) return fail(HZ_ERR_INVALID_ARG, "wave speed not set");
+  if (!pr.has_omega) return fail(HZ_ERR_INVALID_ARG, "omega not set");
+  return HZ_OK;
+}
+
+hz_status prepare(Problem& pr, int nt, cudaStream_t st) {
+  HZ_TRY(check_ready(pr));
+  if (nt < 3) return fail(HZ_ERR_INVALID_ARG, "N_t must be >= 3");
+  if (pr.prepared_nt == nt && pr.prepared_version == pr.version) return HZ_OK;
+  const Geom& g = pr.g;
+  const int64_t nsub = (int64_t)g.L * g.sub_nodes();
+  HZ_TRY(pr.beta64.ensure(nsub * sizeof(double)));
+  HZ_TRY(pr.alpha64.ensure(nsub * sizeof(double)));
+  HZ_TRY(pr.beta32.ensure(nsub * sizeof(float)));
+  HZ_TRY(pr.alpha32.ensure(nsub * sizeof(float)));
+  HZ_TRY(pr.kedge.ensure((size_t)g.lam_complex() * sizeof(double)));
+  const double w = pr.omega;
+  const double dt = (2.0 * M_PI / w) / nt;
+  PrepArgs a{};
+  a.nlx = g.nlx;
+  a.nly = g.nly;
+  a.NE = g.NE;
+  a.Sx = g.Sx;
+  a.Sy = g.Sy;
+  a.NXg = g.NXg;
+  a.snxP = g.snx * g.P;
+  a.snyP = g.sny * g.P;
+  a.theta = std::tan(w * dt / 2.0) / w;
+  a.sigma = std::sin(w * dt / 2.0) / (w / 2.0);
+  a.omega = w;
+  a.c = pr.c.as<double>();
+  a.wxs = pr.wxs.as<double>();
+  a.wys = pr.wys.as<double>();
+  a.beta64 = pr.beta64.as<double>();
+  a.alpha64 = pr.alpha64.as<double>();
+  a.beta32 = pr.beta32.as<float>();
+  a.alpha32 = pr.alpha32.as<float>();
+  a.kedge = pr.kedge.as<double>();
+  HZ_TRY(launch_prepare(a, g.L, st));
+  // filter / forcing tables: nu = 0..Nt: cos, sin of 2 pi nu/Nt, kappa_nu, kappa_{nu+1/2}/omega
+  const double c0 = -0.25 + 0.25 * std::tan(M_PI / nt) * std::tan(M_PI / nt);
+  std::vector<double> t64(4 * (size_t)(nt + 1));
+  std::vector<float> t32(4 * (size_t)(nt + 1));
+  for (int nu = 0; nu <= nt; ++nu) {
+    const double th = 2.0 * M_PI * nu / nt;
+    t64[4 * nu + 0] = std::cos(th);
+    t64[4 * nu + 1] = std::sin(th);
+    t64[4 * nu + 2] = std::cos(th) + c0;
+    t64[4 * nu + 3] = (std::cos(2.0 * M_PI * (nu + 0.5) / nt) + c0) / w;
+    for (int k = 0; k < 4; ++k) t32[4 * nu + k] = (float)t64[4 * nu + k];
+  }
+  HZ_TRY(pr.tab64.ensure(t64.size() * sizeof(double)));
+  HZ_TRY(pr.tab32.ensure(t32.size() * sizeof(float)));
+  HZ_CUDA(cudaMemcpyAsync(pr.tab64.ptr, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  HZ_CUDA(cudaMemcpyAsync(pr.tab32.ptr, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  HZ_CUDA(cudaStreamSynchronize(st));  // host tables go out of scope
+  pr.prepared_nt = nt;
+  pr.prepared_version = pr.version;
+  pr.sigma = a.sigma;
+  return HZ_OK;
+}
+
+hz_status ensure_flags(Problem& pr) {
+  if (!pr.flags.ptr) {
+    HZ_TRY(pr.flags.ensure(64));
+    HZ_CUDA(cudaMemset(pr.flags.ptr, 0, 64));
+  }
+  return HZ_OK;
+}
+
+hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, const double* lam_in, double* lam_out,
+                const double* rhs, double* u_sub, cudaStream_t st) {
+  HZ_TRY(prepare(pr, nt, st));
+  HZ_TRY(ensure_flags(pr));
+  const Geom& g = pr.g;
+  if (m_wh < 0) return fail(HZ_ERR_INVALID_ARG, "wh_iters must be >= 0");
+  const bool fp32 = precision == HZ_FP32_REFINE;
+  if (precision != HZ_FP64 && precision != HZ_FP32_REFINE) return fail(HZ_ERR_INVALID_ARG, "unknown precision");
+  SweepArgs a{};
+  a.nlx = g.nlx;
+  a.nly = g.nly;
+  a.NE = g.NE;
+  a.Sx = g.Sx;
+  a.Sy = g.Sy;
+  a.sxe = g.snx;
+  a.sye = g.sny;
+  a.NXg = g.NXg;
+  a.snxP = g.snx * g.P;
+  a.snyP = g.sny * g.P;
+  a.Nt = nt;
+  a.m_wh = m_wh;
+  a.wh_tol = wh_tol;
+  a.sigma = pr.sigma;
+  a.omega = pr.omega;
+  a.cpi = std::cos(M_PI / nt);
+  a.spi = std::sin(M_PI / nt);
+  a.two_over_nt = 2.0 / nt;
+  a.kxs = 2.0 / g.hx;
+  a.kys = 2.0 / g.hy;
+  a.hx2 = g.hx / 2.0;
+  a.hy2 = g.hy / 2.0;
+  for (size_t k = 0; k < g.Kref.size(); ++k) {
+    a.Kref[k] = g.Kref[k];
+    a.Kref32[k] = (float)g.Kref[k];
+  }
+  for (int k = 0; k <= g.P; ++k) a.w[k] = g.w[k];
+  a.beta = fp32 ? pr.beta32.ptr : pr.beta64.ptr;
+  a.alpha = fp32 ? pr.alpha32.ptr : pr.alpha64.ptr;
+  a.tab = fp32 ? pr.tab32.ptr : pr.tab64.ptr;
+  a.kedge = pr.kedge.as<double>();
+  a.wxs = pr.wxs.as<double>();
+  a.wys = pr.wys.as<double>();
+  a.rhs = rhs;
+  a.lam_in = lam_in;
+  a.lam_out = lam_out;
+  a.u_sub = u_sub;
+  int* fl = pr.flags.as<int>();
+  a.flags = fl;
+  a.wh_iter_max = fl + 1;
+  a.wh_iter_sum = reinterpret_cast<unsigned long long*>(fl + 2);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (pr.time_sweeps) {
+    if (pr.ev_used + 2 > pr.events.size()) {
+      for (int k = 0; k < 2; ++k) {
+        cudaEvent_t e;
+        HZ_CUDA(cudaEventCreate(&e));
+        pr.events.push_back(e);
+      }
+    }
+    e0 = pr.events[pr.ev_used];
+    e1 = pr.events[pr.ev_used + 1];
+    pr.ev_used += 2;
+    HZ_CUDA(cudaEventRecord(e0, st));
+  }
+  HZ_TRY(launch_sweep(fp32, g.P, a, g.L, st));
+  if (e1) HZ_CUDA(cudaEventRecord(e1, st));
+  pr.sweeps_launched++;
+  return HZ_OK;
+}
+
+hz_status residual(Problem& pr, const double* b, const double* u, double* r, double* norms2_dev, cudaStream_t st) {
+  HZ_TRY(check_ready(pr));
+  const GlobalArgs a = global_args(pr);
+  const int nb = residual_blocks(a);
+  HZ_TRY(pr.part.ensure((size_t)std::max(nb, 1) * 2 * sizeof(double)));
+  int used = 0;
+  HZ_TRY(launch_residual(a, b, u, r, pr.part.as<double>(), &used, st));
+  if (norms2_dev) HZ_TRY(launch_reduce_partials(pr.part.as<double>(), used, 2, norms2_dev, st));
+  return HZ_OK;
+}
+
+hz_status rhs(Problem& pr, double* b, cudaStream_t st) {
+  HZ_TRY(check_ready(pr));
+  const GlobalArgs a = global_args(pr);
+  return launch_rhs(a, pr.f.as<double>(), pr.gb.as<double>(), b, st);
+}
+
+hz_status assemble_add(Problem& pr, const double* u_sub, double* u, cudaStream_t st) {
+  const Geom& g = pr.g;
+  AssembleArgs a{};
+  a.nlx = g.nlx;
+  a.nly = g.nly;
+  a.Sx = g.Sx;
+  a.Sy = g.Sy;
+  a.NXg = g.NXg;
+  a.NYg = g.NYg;
+  a.snxP = g.snx * g.P;
+  a.snyP = g.sny * g.P;
+  return launch_assemble_add(a, u_sub, u, st);
+}
+
+// ------------------------------------------------------- outer iteration ----
+namespace {
+
+using cplx = std::complex<double>;
+constexpr double kGrowthLimit = 1e8;      // see the GMRES loop
+constexpr double kResidualGrowth = 1e4;   // refinement step that multiplies the residual by this diverged
+
+struct Ctx {
+  Problem& pr;
+  const hz_solve_opts& o;
+  int nt;
+  cudaStream_t st;
+  hz_solve_report& rep;
+  int64_t n2;  // doubles in a lambda vector
+};
+
+// Reads nd doubles from device small-buffer offset 0 and the flag words.
+hz_status fetch(Ctx& c, int nd, double* host, int* flags_host) {
+  Problem& pr = c.pr;
+  HZ_CUDA(cudaMemcpyAsync(pr.hsmall.ptr, pr.small.ptr, (size_t)nd * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+  HZ_CUDA(cudaMemcpyAsync(static_cast<char*>(pr.hsmall.ptr) + 4096 * sizeof(double), pr.flags.ptr, 16,
+                          cudaMemcpyDeviceToHost, c.st));
+  HZ_CUDA(cudaStreamSynchronize(c.st));
+  std::memcpy(host, pr.hsmall.ptr, (size_t)nd * sizeof(double));
+  std::memcpy(flags_host, static_cast<char*>(pr.hsmall.ptr) + 4096 * sizeof(double), 16);
+  if (flags_host[0] & 1) return fail(HZ_ERR_DIVERGED, "non-finite values in the subdomain solve (time step too large?)");
+  for (int k = 0; k < nd; ++k)
+    if (!std::isfinite(host[k])) return fail(HZ_ERR_DIVERGED, "non-finite value in the outer iteration");
+  return HZ_OK;
+}
+
+// out[0..2nv) = reduced dots of V_0..V_{nv-1} with w (device small buffer at offset off).
+hz_status dots(Ctx& c, const double* V, int64_t ld, int nv, const double* w, bool real, int off) {
+  Problem& pr = c.pr;
+  const int nb = vec_blocks(c.n2);
+  HZ_TRY(pr.part.ensure((size_t)nb * nv * 2 * sizeof(double) + 64));
+  HZ_TRY(launch_multi_dot(V, ld, nv, w, c.n2, real, pr.part.as<double>(), nb, c.st));
+  return launch_reduce_partials(pr.part.as<double>(), nb, 2 * nv, pr.small.as<double>() + off, c.st);
+}
+
+// Outer-iteration sweeps keep one sweep of the budget in reserve for the
+// closing sweep of the DD solve (reserve = 1); the closing sweep uses 0.
+hz_status do_sweep(Ctx& c, const double* lam_in, double* lam_out, const double* rhs, double* u_sub, int reserve = 1) {
+  if (c.rep.sweeps + reserve >= c.o.max_sweeps) return fail(HZ_ERR_NOT_CONVERGED, "sweep budget exhausted");
+  HZ_TRY(sweep(c.pr, c.o.precision, c.nt, c.o.wh_iters, c.o.wh_tol, lam_in, lam_out, rhs, u_sub, c.st));
+  c.rep.sweeps++;
+  return HZ_OK;
+}
+
+// Approximate K^{-1} rhs by the DD method and add it to u.
+hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
+  Problem& pr = c.pr;
+  const Geom& g = pr.g;
+  const int64_t n2 = c.n2;
+  const size_t vb = (size_t)n2 * sizeof(double);
+  const int m = std::max(1, c.o.gmres_restart);
+  const bool real = c.o.outer == HZ_OUTER_RGMRES;
+  HZ_TRY(pr.gv.ensure(vb));
+  HZ_TRY(pr.xv.ensure(vb));
+  HZ_TRY(pr.tv.ensure(vb));
+  HZ_TRY(pr.usub.ensure((size_t)g.L * g.sub_nodes() * 2 * sizeof(double)));
+  HZ_TRY(pr.small.ensure(8192 * sizeof(double)));
+  HZ_TRY(pr.hsmall.ensure(8192 * sizeof(double)));
+  double* gv = pr.gv.as<double>();
+  double* xv = pr.xv.as<double>();
+  double* tv = pr.tv.as<double>();
+  HZ_CUDA(cudaMemsetAsync(xv, 0, vb, c.st));
+  // g = T(0): sweep with zero transmission data and the source
+  HZ_TRY(do_sweep(c, xv, gv, rhs, nullptr));
+  int flags[4];
+  double hbuf[8192];
+  HZ_TRY(dots(c, gv, 0, 1, gv, real, 0));
+  HZ_TRY(fetch(c, 2, hbuf, flags));
+  const double gnorm = std::sqrt(hbuf[0]);
+  const double tol = c.o.inner_tol;
+  if (gnorm > 0.0) {
+    if (c.o.outer == HZ_OUTER_PLAIN) {
+      // lambda <- S(lambda) + g, i.e. a sweep with the source (eq. (lambda-iteration))
+      HZ_CUDA(cudaMemcpyAsync(xv, gv, vb, cudaMemcpyDeviceToDevice, c.st));
+      while (true) {
+        hz_status s = do_sweep(c, xv, tv, rhs, nullptr);
+        if (s == HZ_ERR_NOT_CONVERGED) break;
+        HZ_TRY(s);
+        HZ_TRY(launch_axpby(1.0, tv, -1.0, xv, n2, c.st));  // xv = tv - xv (difference)
+        HZ_TRY(dots(c, xv, 0, 1, xv, true, 0));
+        HZ_TRY(fetch(c, 2, hbuf, flags));
+        if (!(std::sqrt(hbuf[0]) < kGrowthLimit * gnorm))
+          return fail(HZ_ERR_DIVERGED, "fixed-point iteration exploded: time step beyond the stability limit?");
+        HZ_CUDA(cudaMemcpyAsync(xv, tv, vb, cudaMemcpyDeviceToDevice, c.st));
+        c.rep.gmres_iters++;
+        if (std::sqrt(hbuf[0]) <= tol * gnorm) break;
+      }
+    } else {
+      HZ_TRY(pr.V.ensure(vb * (m + 1)));
+      double* V = pr.V.as<double>();
+      std::vector<cplx> H((size_t)(m + 1) * m), cs(m), sn(m), gvec(m + 1);
+      bool first = true, done = false;
+      while (!done) {
+        // residual of the current iterate into V_0
+        if (first) {
+          HZ_CUDA(cudaMemcpyAsync(V, gv, vb, cudaMemcpyDeviceToDevice, c.st));
+          first = false;
+        } else {
+          hz_status s = do_sweep(c, xv, tv, nullptr, nullptr);
+          if (s == HZ_ERR_NOT_CONVERGED) break;
+          HZ_TRY(s);
+          // V0 = g - (x - S x) = g - x + t
+          HZ_CUDA(cudaMemcpyAsync(V, gv, vb, cudaMemcpyDeviceToDevice, c.st));
+          HZ_TRY(launch_axpby(-1.0, xv, 1.0, V, n2, c.st));
+          HZ_TRY(launch_axpby(1.0, tv, 1.0, V, n2, c.st));
+        }
+        HZ_TRY(dots(c, V, 0, 1, V, real, 0));
+        HZ_TRY(fetch(c, 2, hbuf, flags));
+        const double beta = std::sqrt(hbuf[0]);
+        if (beta <= tol * gnorm) break;
+        HZ_TRY(launch_axpby(0.0, V, 1.0 / beta, V, n2, c.st));
+        std::fill(gvec.begin(), gvec.end(), cplx(0.0));
+        gvec[0] = beta;
+        int k = 0;
+        for (int j = 0; j < m; ++j) {
+          double* vj = V + (size_t)j * n2;
+          double* w = V + (size_t)(j + 1) * n2;
+          hz_status s = do_sweep(c, vj, tv, nullptr, nullptr);
+          if (s == HZ_ERR_NOT_CONVERGED) { done = true; break; }
+          HZ_TRY(s);
+          // w = v_j - S v_j
+          HZ_CUDA(cudaMemcpyAsync(w, vj, vb, cudaMemcpyDeviceToDevice, c.st));
+          HZ_TRY(launch_axpby(-1.0, tv, 1.0, w, n2, c.st));
+          // classical Gram-Schmidt, two passes
+          const int nv = j + 1;
+          HZ_TRY(dots(c, V, n2, nv, w, real, 0));
+          HZ_TRY(launch_multi_axpy(V, n2, nv, pr.small.as<double>(), w, n2, real, c.st));
+          HZ_TRY(dots(c, V, n2, nv, w, real, 2 * (m + 1)));
+          HZ_TRY(launch_multi_axpy(V, n2, nv, pr.small.as<double>() + 2 * (m + 1), w, n2, real, c.st));
+          HZ_TRY(dots(c, w, 0, 1, w, real, 4 * (m + 1)));
+          HZ_TRY(fetch(c, 4 * (m + 1) + 2, hbuf, flags));
+          c.rep.gmres_iters++;
+          for (int i = 0; i <= j; ++i)
+            H[(size_t)i * m + j] = cplx(hbuf[2 * i] + hbuf[2 * (m + 1) + 2 * i],
+                                        hbuf[2 * i + 1] + hbuf[2 * (m + 1) + 2 * i + 1]);
+          const double hnext = std::sqrt(std::max(0.0, hbuf[4 * (m + 1)]));
+          // ||(I - S) v|| for a unit v is O(1) for a stable subdomain solve; growth by
+          // many orders of magnitude means the leapfrog is unstable (time step too large)
+          if (!(hnext < kGrowthLimit) || !(std::abs(H[(size_t)j * m + j]) < kGrowthLimit))
+            return fail(HZ_ERR_DIVERGED, "sweep operator norm exploded: time step beyond the stability limit?");
+          // apply previous rotations
+          for (int i = 0; i < j; ++i) {
+            const cplx a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
+            H[(size_t)i * m + j] = cs[i] * a + sn[i] * b;
+            H[(size_t)(i + 1) * m + j] = -std::conj(sn[i]) * a + cs[i] * b;
+          }
+          const cplx a = H[(size_t)j * m + j];
+          const double r = std::sqrt(std::norm(a) + hnext * hnext);
+          if (std::abs(a) == 0.0) {
+            cs[j] = 0.0;
+            sn[j] = 1.0;
+          } else {
+            cs[j] = std::abs(a) / r;
+            sn[j] = (a / std::abs(a)) * hnext / r;
+          }
+          H[(size_t)j * m + j] = cs[j] * a + sn[j] * hnext;
+          gvec[j + 1] = -std::conj(sn[j]) * gvec[j];
+          gvec[j] = cs[j] * gvec[j];
+          k = j + 1;
+          const double res = std::abs(gvec[j + 1]);
+          if (res <= tol * gnorm || hnext == 0.0) { done = true; break; }
+          if (c.rep.sweeps + 1 >= c.o.max_sweeps) { done = true; break; }
+          HZ_TRY(launch_axpby(0.0, w, 1.0 / hnext, w, n2, c.st));
+        }
+        if (k > 0) {
+          // back substitution R y = gvec, then x += V y  (multi_axpy subtracts, so pass -y)
+          std::vector<cplx> y(k);
+          for (int i = k - 1; i >= 0; --i) {
+            cplx s = gvec[i];
+            for (int q = i + 1; q < k; ++q) s -= H[(size_t)i * m + q] * y[q];
+            y[i] = s / H[(size_t)i * m + i];
+          }
+          std::vector<double> ny(2 * k);
+          for (int i = 0; i < k; ++i) {
+            ny[2 * i] = -y[i].real();
+            ny[2 * i + 1] = real ? 0.0 : -y[i].imag();
+          }
+          HZ_CUDA(cudaMemcpyAsync(pr.small.ptr, ny.data(), ny.size() * sizeof(double), cudaMemcpyHostToDevice, c.st));
+          HZ_TRY(launch_multi_axpy(V, n2, k, pr.small.as<double>(), xv, n2, real, c.st));
+          HZ_CUDA(cudaStreamSynchronize(c.st));  // ny leaves scope
+        }
+      }
+    }
+  }
+  // final sweep at the converged transmission data: subdomain solutions -> u
+  hz_solve_opts relaxed = c.o;
+  relaxed.max_sweeps = std::max(c.o.max_sweeps, c.rep.sweeps + 1);  // the closing sweep is always allowed
+  Ctx cf{pr, relaxed, c.nt, c.st, c.rep, c.n2};
+  HZ_TRY(do_sweep(cf, xv, tv, rhs, pr.usub.as<double>(), 0));
+  HZ_TRY(assemble_add(pr, pr.usub.as<double>(), u, c.st));
+  return HZ_OK;
+}
+
+}  // namespace
+
+hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report* rep_out, cudaStream_t st) {
+  const auto t0 = std::chrono::steady_clock::now();
+  HZ_TRY(check_ready(pr));
+  if (!(o.tol >= 0.0) || o.max_sweeps < 1 || o.gmres_restart < 1 || o.gmres_restart > 1000 || o.wh_iters < 1 ||
+      !(o.cfl > 0.0) || o.max_refine < 0 || !(o.inner_tol >= 0.0) || !(o.wh_tol >= 0.0))
+    return fail(HZ_ERR_INVALID_ARG, "invalid solve options");
+  if (o.outer < HZ_OUTER_GMRES || o.outer > HZ_OUTER_RGMRES) return fail(HZ_ERR_INVALID_ARG, "unknown outer");
+  hz_solve_report rep{};
+  const int nt = o.nt_override > 0 ? o.nt_override : choose_nt(pr, o.cfl);
+  rep.nt = nt;
+  const Geom& g = pr.g;
+  const size_t nb = (size_t)g.n * 2 * sizeof(double);
+  HZ_TRY(pr.bvec.ensure(nb));
+  HZ_TRY(pr.rvec.ensure(nb));
+  HZ_TRY(pr.small.ensure(8192 * sizeof(double)));
+  HZ_TRY(pr.hsmall.ensure(8192 * sizeof(double)));
+  HZ_TRY(prepare(pr, nt, st));
+  HZ_TRY(ensure_flags(pr));
+  HZ_CUDA(cudaMemsetAsync(pr.flags.ptr, 0, 64, st));
+  HZ_TRY(rhs(pr, pr.bvec.as<double>(), st));
+  HZ_CUDA(cudaMemsetAsync(u, 0, nb, st));
+  Ctx c{pr, o, nt, st, rep, 2 * g.lam_complex()};
+  pr.time_sweeps = true;
+  pr.ev_used = 0;
+  struct TimingOff {  // direct hz_sweep calls after a failed solve record nothing
+    Problem& p;
+    ~TimingOff() { p.time_sweeps = false; }
+  } timing_off{pr};
+  double hb[4];
+  int flags[4];
+  hz_status result = HZ_OK;
+  double bnorm = 0.0;
+  while (true) {
+    HZ_TRY(residual(pr, pr.bvec.as<double>(), u, pr.rvec.as<double>(), pr.small.as<double>(), st));
+    HZ_TRY(fetch(c, 2, hb, flags));
+    bnorm = std::sqrt(hb[1]);
+    const double rel = bnorm > 0.0 ? std::sqrt(hb[0]) / bnorm : 0.0;
+    if (rep.refinements > 0 && !(rel < kResidualGrowth * rep.rel_residual)) {
+      rep.rel_residual = rel;
+      if (rep_out) *rep_out = rep;
+      return fail(HZ_ERR_DIVERGED, "refinement step increased the residual by orders of magnitude");
+    }
+    rep.rel_residual = rel;
+    if (rel <= o.tol) break;
+    if (rep.refinements >= o.max_refine || rep.sweeps + 2 > o.max_sweeps) {  // a DD solve needs >= 2 sweeps
+      result = fail(HZ_ERR_NOT_CONVERGED, "tolerance not reached within the refinement / sweep budget");
+      break;
+    }
+    hz_status s = dd_solve(c, pr.rvec.as<double>(), u);
+    if (s != HZ_OK && s != HZ_ERR_NOT_CONVERGED) return s;
+    rep.refinements++;
+  }
+  HZ_CUDA(cudaMemcpyAsync(flags, pr.flags.ptr, 16, cudaMemcpyDeviceToHost, st));
+  HZ_CUDA(cudaStreamSynchronize(st));
+  unsigned long long itsum = 0;
+  std::memcpy(&itsum, &flags[2], sizeof(itsum));
+  rep.wh_iters_max = flags[1];
+  rep.dof_updates = (int64_t)itsum * g.sub_nodes() * (nt - 1);
+  double sw = 0.0;
+  for (size_t k = 0; k + 1 < pr.ev_used; k += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pr.events[k], pr.events[k + 1]) == cudaSuccess) sw += ms * 1e-3;
+  }
+  (void)cudaGetLastError();
+  rep.sweep_seconds = sw;
+  pr.time_sweeps = false;
+  rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (rep_out) *rep_out = rep;
+  return result;
+}
+
+}  // namespace hz
+
+// =========================================================== C ABI ====
+using namespace hz;
+
+namespace {
+template <typename F>
+hz_status guard(F&& f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    return fail(HZ_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(HZ_ERR_INTERNAL, e.what());
+  } catch (...) {
+    return fail(HZ_ERR_INTERNAL, "unknown exception");
+  }
+}
+
+hz_status use_device(const Problem& pr) {
+  HZ_CUDA(cudaSetDevice(pr.device));
+  return HZ_OK;
+}
+
+bool all_finite(const double* p, int64_t n) {
+  for (int64_t k = 0; k < n; ++k)
+    if (!std::isfinite(p[k])) return false;
+  return true;
+}
+
+int64_t field_count(const Geom& g, hz_field f) {
+  switch (f) {
+    case HZ_WAVE_SPEED: return g.n;
+    case HZ_OMEGA: return 1;
+    case HZ_SOURCE: return g.n;
+    case HZ_BOUNDARY: return 2 * (int64_t)g.NXg + 2 * (int64_t)g.NYg;
+  }
+  return -1;
+}
+
+hz_status set_field_host(Problem& pr, hz_field field, const double* data, int64_t count) {
+  const Geom& g = pr.g;
+  if (!data) return fail(HZ_ERR_INVALID_ARG, "null data");
+  const int64_t want = field_count(g, field);
+  if (want < 0) return fail(HZ_ERR_INVALID_ARG, "unknown field");
+  if (count != want) return fail(HZ_ERR_INVALID_ARG, "wrong value count for field");
+  const bool cplx_field = field == HZ_SOURCE || field == HZ_BOUNDARY;
+  const int64_t nd = cplx_field ? 2 * count : count;
+  if (!all_finite(data, nd)) return fail(HZ_ERR_INVALID_ARG, "non-finite input");
+  HZ_TRY(use_device(pr));
+  switch (field) {
+    case HZ_WAVE_SPEED: {
+      double cmax = 0.0;
+      for (int64_t k = 0; k < count; ++k) {
+        if (!(data[k] > 0.0)) return fail(HZ_ERR_INVALID_ARG, "wave speed must be > 0");
+        cmax = std::max(cmax, data[k]);
+      }
+      HZ_TRY(pr.c.ensure(nd * sizeof(double)));
+      HZ_CUDA(cudaMemcpy(pr.c.ptr, data, nd * sizeof(double), cudaMemcpyHostToDevice));
+      pr.cmax = cmax;
+      pr.has_c = true;
+      break;
+    }
+    case HZ_OMEGA:
+      if (!(data[0] > 0.0)) return fail(HZ_ERR_INVALID_ARG, "omega must be > 0");
+      pr.omega = data[0];
+      pr.has_omega = true;
+      break;
+    case HZ_SOURCE:
+      HZ_TRY(pr.f.ensure(nd * sizeof(double)));
+      HZ_CUDA(cudaMemcpy(pr.f.ptr, data, nd * sizeof(double), cudaMemcpyHostToDevice));
+      break;
+    case HZ_BOUNDARY:
+      HZ_TRY(pr.gb.ensure(nd * sizeof(double)));
+      HZ_CUDA(cudaMemcpy(pr.gb.ptr, data, nd * sizeof(double), cudaMemcpyHostToDevice));
+      break;
+  }
+  pr.version++;
+  return HZ_OK;
+}
+
+hz_status opts_or_default(const hz_solve_opts* o, hz_solve_opts* out) {
+  if (o) *out = *o;
+  else hz_default_opts(out);
+  return HZ_OK;
+}
+}  // namespace
+
+extern "C" {
+
+hz_status hz_kernel_launches(uint64_t* count) {
+  if (!count) return fail(HZ_ERR_INVALID_ARG, "null argument");
+  *count = g_launches.load();
+  return HZ_OK;
+}
+
+void hz_default_opts(hz_solve_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = HZ_FP64;
+  o->tol = 1e-8;
+  o->max_sweeps = 2000;
+  o->outer = HZ_OUTER_GMRES;
+  o->gmres_restart = 60;
+  o->wh_iters = 10;
+  o->wh_tol = 0.0;
+  o->nt_override = 0;
+  o->cfl = 0.9;
+  o->inner_tol = 1e-6;
+  o->max_refine = 20;
+}
+
+hz_status hz_last_error(char* buf, size_t n) {
+  if (!buf || n == 0) return HZ_ERR_INVALID_ARG;
+  std::strncpy(buf, g_last_error.c_str(), n - 1);
+  buf[n - 1] = '\0';
+  return HZ_OK;
+}
+
+hz_status hz_mesh_create(double x0, double x1, double y0, double y1, int32_t nx, int32_t ny, int32_t degree,
+                         int32_t sub_nx, int32_t sub_ny, hz_mesh* out) {
+  return guard([&]() -> hz_status {
+    if (!out) return fail(HZ_ERR_INVALID_ARG, "null output handle");
+    *out = nullptr;
+    auto* m = new hz_mesh_s();
+    hz_status s = build_geom(x0, x1, y0, y1, nx, ny, degree, sub_nx, sub_ny, &m->g);
+    if (s != HZ_OK) {
+      delete m;
+      return s;
+    }
+    *out = m;
+    return HZ_OK;
+  });
+}
+
+hz_status hz_mesh_num_nodes(hz_mesh mesh, int64_t* n) {
+  if (!mesh || !n) return fail(HZ_ERR_INVALID_ARG, "null argument");
+  *n = mesh->g.n;
+  return HZ_OK;
+}
+
+hz_status hz_mesh_node_coords(hz_mesh mesh, double* xy) {
+  if (!mesh || !xy) return fail(HZ_ERR_INVALID_ARG, "null argument");
+  const Geom& g = mesh->g;
+  for (int J = 0; J < g.NYg; ++J) {
+    const int ey = std::min(J / g.P, g.ny - 1), b = J - ey * g.P;
+    const double y = g.y0 + ey * g.hy + (g.xi[b] + 1.0) * g.hy / 2.0;
+    for (int I = 0; I < g.NXg; ++I) {
+      const int ex = std::min(I / g.P, g.nx - 1), a = I - ex * g.P;
+      const double x = g.x0 + ex * g.hx + (g.xi[a] + 1.0) * g.hx / 2.0;
+      xy[2 * ((int64_t)J * g.NXg + I)] = x;
+      xy[2 * ((int64_t)J * g.NXg + I) + 1] = y;
+    }
+  }
+  return HZ_OK;
+}
+
+void hz_mesh_destroy(hz_mesh mesh) { delete mesh; }
+
+hz_status hz_problem_create(hz_mesh mesh, int32_t device, hz_problem* out) {
+  return guard([&]() -> hz_status {
+    if (!mesh || !out) return fail(HZ_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    int ndev = 0;
+    HZ_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(HZ_ERR_INVALID_ARG, "no such CUDA device");
+    auto* pr = new hz_problem_s();
+    pr->g = mesh->g;
+    pr->device = device;
+    hz_status s = [&]() -> hz_status {
+      HZ_CUDA(cudaSetDevice(device));
+      const Geom& g = pr->g;
+      HZ_TRY(pr->Wxg.ensure(g.Wxg.size() * sizeof(double)));
+      HZ_TRY(pr->Wyg.ensure(g.Wyg.size() * sizeof(double)));
+      HZ_TRY(pr->wxs.ensure(g.Wxs.size() * sizeof(double)));
+      HZ_TRY(pr->wys.ensure(g.Wys.size() * sizeof(double)));
+      HZ_CUDA(cudaMemcpy(pr->Wxg.ptr, g.Wxg.data(), g.Wxg.size() * sizeof(double), cudaMemcpyHostToDevice));
+      HZ_CUDA(cudaMemcpy(pr->Wyg.ptr, g.Wyg.data(), g.Wyg.size() * sizeof(double), cudaMemcpyHostToDevice));
+      HZ_CUDA(cudaMemcpy(pr->wxs.ptr, g.Wxs.data(), g.Wxs.size() * sizeof(double), cudaMemcpyHostToDevice));
+      HZ_CUDA(cudaMemcpy(pr->wys.ptr, g.Wys.data(), g.Wys.size() * sizeof(double), cudaMemcpyHostToDevice));
+      // source and boundary default to zero
+      HZ_TRY(pr->f.ensure((size_t)g.n * 2 * sizeof(double)));
+      HZ_CUDA(cudaMemset(pr->f.ptr, 0, (size_t)g.n * 2 * sizeof(double)));
+      const size_t nbd = (size_t)(2 * g.NXg + 2 * g.NYg) * 2 * sizeof(double);
+      HZ_TRY(pr->gb.ensure(nbd));
+      HZ_CUDA(cudaMemset(pr->gb.ptr, 0, nbd));
+      HZ_CUDA(cudaStreamCreateWithFlags(&pr->stream, cudaStreamNonBlocking));
+      return HZ_OK;
+    }();
+    if (s != HZ_OK) {
+      delete pr;
+      return s;
+    }
+    *out = pr;
+    return HZ_OK;
+  });
+}
+
+hz_status hz_problem_set(hz_problem pr, hz_field field, const double* data, int64_t count) {
+  if (!pr) return fail(HZ_ERR_INVALID_ARG, "null problem");
+  return guard([&]() { return set_field_host(*pr, field, data, count); });
+}
+
+hz_status hz_problem_set_device(hz_problem pr, hz_field field, const double* data, int64_t count, void* stream) {
+  if (!pr || !data) return fail(HZ_ERR_INVALID_ARG, "null argument");
+  return guard([&]() -> hz_status {
+    const int64_t want = field_count(pr->g, field);
+    if (want < 0 || count != want) return fail(HZ_ERR_INVALID_ARG, "wrong value count for field");
+    const bool cplx_field = field == HZ_SOURCE || field == HZ_BOUNDARY;
+    const int64_t nd = cplx_field ? 2 * count : count;
+    // validate on the host (the check reads the data once; the copy stays device-side)
+    std::vector<double> tmp((size_t)nd);
+    HZ_TRY(use_device(*pr));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    HZ_CUDA(cudaMemcpyAsync(tmp.data(), data, nd * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HZ_CUDA(cudaStreamSynchronize(st));
+    if (field == HZ_OMEGA || field == HZ_WAVE_SPEED) return set_field_host(*pr, field, tmp.data(), count);
+    if (!all_finite(tmp.data(), nd)) return fail(HZ_ERR_INVALID_ARG, "non-finite input");
+    DevBuf& dst = field == HZ_SOURCE ? pr->f : pr->gb;
+    HZ_TRY(dst.ensure(nd * sizeof(double)));
+    HZ_CUDA(cudaMemcpyAsync(dst.ptr, data, nd * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    HZ_CUDA(cudaStreamSynchronize(st));
+    pr->version++;
+    return HZ_OK;
+  });
+}
+
+void hz_problem_destroy(hz_problem pr) {
+  if (!pr) return;
+  cudaSetDevice(pr->device);
+  for (cudaEvent_t e : pr->events) cudaEventDestroy(e);
+  if (pr->stream) cudaStreamDestroy(pr->stream);
+  delete pr;
+}
+
+hz_status hz_problem_nt(hz_problem pr, double cfl, int32_t* nt) {
+  if (!pr || !nt) return fail(HZ_ERR_INVALID_ARG, "null argument");
+  return guard([&]() -> hz_status {
+    HZ_TRY(check_ready(*pr));
+    if (!(cfl > 0.0)) return fail(HZ_ERR_INVALID_ARG, "cfl must be > 0");
+    *nt = choose_nt(*pr, cfl);
+    return HZ_OK;
+  });
+}
+
+hz_status hz_solve(hz_problem pr, const hz_solve_opts* opts, double* u_out, hz_solve_report* report) {
+  if (!pr || !u_out) return fail(HZ_ERR_INVALID_ARG, "null argument");
+  return guard([&]() -> hz_status {
+    HZ_TRY(use_device(*pr));
+    hz_solve_opts o;
+    opts_or_default(opts, &o);
+    const size_t nb = (size_t)pr->g.n * 2 * sizeof(double);
+    HZ_TRY(pr->uvec.ensure(nb));
+    hz_status s = solve(*pr, o, pr->uvec.as<double>(), report, pr->stream);
+    if (s != HZ_OK && s != HZ_ERR_NOT_CONVERGED) return s;
+    HZ_CUDA(cudaMemcpyAsync(u_out, pr->uvec.ptr, nb, cudaMemcpyDeviceToHost, pr->stream));
+    HZ_CUDA(cudaStreamSynchronize(pr->stream));
+    return s;
+  });
+}
+
+hz_status hz_solve_device(hz_problem pr, const hz_solve_opts* opts, double* u_out_dev, hz_solve_report* report,
+                          void* stream) {
+  if (!pr || !u_out_dev) return fail(HZ_ERR_INVALID_ARG, "null argument");
+  return guard([&]() -> hz_status {
+    HZ_TRY(use_device(*pr));
+    hz_solve_opts o;
+    opts_or_default(opts, &o);
+    return solve(*pr, o, u_out_dev, report, static_cast<cudaStream_t>(stream));
+  });
+}
+
+hz_status hz_lambda_size(hz_problem pr, int64_t* n) {
+  if (!pr || !n) return fail(HZ_ERR_INVALID_ARG, "null argument");
+  *n = pr->g.lam_complex();
+  return HZ_OK;
+}
+
+hz_status hz_prepare(hz_problem pr, int32_t nt, void* stream) {
+  if (!pr) return fail(HZ_ERR_INVALID_ARG, "null problem");
+  return guard([&]() -> hz_status {
+    HZ_TRY(use_device(*pr));
+    return prepare(*pr, nt, static_cast<cudaStream_t>(stream));
+  });
+}
+
+hz_status hz_sweep(hz_problem pr, int32_t precision, int32_t nt, int32_t wh_iters, double wh_tol,
+                   const double* lam_in, double* lam_out, const double* rhs_dev, double* u_sub, void* stream) {
+  if (!pr || !lam_in || !lam_out) return fail(HZ_ERR_INVALID_ARG, "null argument");
+  if (lam_in == lam_out) return fail(HZ_ERR_INVALID_ARG, "lam_in and lam_out must not alias");
+  return guard([&]() -> hz_status {
+    HZ_TRY(use_device(*pr));
+    return sweep(*pr, precision, nt, wh_iters, wh_tol, lam_in, lam_out, rhs_dev, u_sub,
+                 static_cast<cudaStream_t>(stream));
+  });
+}
+
+hz_status hz_rhs(hz_problem pr, double* b, void* stream) {
+  if (!pr || !b) return fail(HZ_ERR_INVALID_ARG, "null argument");
+  return guard([&]() -> hz_status {
+    HZ_TRY(use_device(*pr));
+    return rhs(*pr, b, static_cast<cudaStream_t>(stream));
+  });
+}
+
+hz_status hz_residual(hz_problem pr, const double* b, const double* u, double* r, double* norms2, void* stream) {
+  if (!pr || !u || !r) return fail(HZ_ERR_INVALID_ARG, "null argument");
+  return guard([&]() -> hz_status {
+    HZ_TRY(use_device(*pr));
+    return residual(*pr, b, u, r, norms2, static_cast<cudaStream_t>(stream));
+  });
+}
+
+hz_status hz_assemble_add(hz_problem pr, const double* u_sub, double* u, void* stream) {
+  if (!pr || !u_sub || !u) return fail(HZ_ERR_INVALID_ARG, "null argument");
+  return guard([&]() -> hz_status {
+    HZ_TRY(use_device(*pr));
+    return assemble_add(*pr, u_sub, u, static_cast<cudaStream_t>(stream));
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,320 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, on
+the same seeded inputs (each side evaluates the generators at its own node
+coordinates).
+
+Tolerances:
+* FP64 kernels vs oracle: 1e-12 relative to the largest entry (same
+  arithmetic, different summation order: the kernel uses the assembled
+  tensor-product stiffness, the oracle the element-by-element form).
+* FP32 sweep vs FP64 oracle: 2e-4 relative.  Derivation: the WaveHoltz loop
+  runs (N_t - 1) m_wh leapfrog steps; each step adds O(eps_32 = 6e-8)
+  relative rounding to p and p-dot, and the filter sum accumulates N_t terms,
+  so the error grows like eps_32 * N_t * m_wh ~ 6e-8 * 80 * 5 = 2.4e-5; the
+  bound keeps a factor of ~8 margin.
+* solutions: the solve stops on the global FP64 residual; the error against
+  the direct solve is bounded by cond(K) * residual, checked at 1e-10 with a
+  1e-12 residual target on these small meshes.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dd, sem
+from workloads import configs
+
+pytestmark = pytest.mark.gpu
+
+
+def _wl(nx, ny, sx, sy, P, omega=9.0, kind="random", box=(0.0, 1.0, 0.0, 1.0)):
+    return configs.Workload(f"t{nx}x{ny}p{P}", box, nx, ny, P, sx, sy, omega, kind, (0.37, 0.58), 0.08,
+                            corr_len=0.3)
+
+
+def _pair(hz, wl, g_seed=None):
+    from paper_2606_21695_gb300.api import Case
+
+    case = Case(wl, device=0)
+    m = sem.Mesh(*wl.box, wl.nx, wl.ny, wl.P, wl.sub_nx, wl.sub_ny)
+    gx, gy = m.coords_1d()
+    g = wl.boundary()
+    if g_seed is not None:
+        rng = np.random.default_rng(g_seed)
+        g = {k: rng.standard_normal(len(v)) + 1j * rng.standard_normal(len(v)) for k, v in g.items()}
+        from paper_2606_21695_gb300.api import boundary_vector
+
+        hz.hz_problem_set(case.pr, hz.HZ_BOUNDARY, boundary_vector(g))
+    pr = dd.Problem(m, wl.speed(gx, gy), wl.omega, wl.source(gx, gy), g)
+    # inputs agree (generators evaluated at each side's own coordinates)
+    assert np.max(np.abs(case.c - pr.c)) < 1e-12
+    return case, pr
+
+
+def _rand_lam(pr, seed):
+    m = pr.mesh
+    rng = np.random.default_rng(seed)
+    lam = rng.standard_normal((m.L, 4, m.NE)) + 1j * rng.standard_normal((m.L, 4, m.NE))
+    for l in range(m.L):
+        for e in range(4):
+            if pr.nbr[l, e] < 0:
+                lam[l, e] = 0
+            else:
+                n = m.nly if e < 2 else m.nlx
+                lam[l, e, n:] = 0
+    return lam
+
+
+def _dev(x):
+    import torch
+
+    a = np.ascontiguousarray(x)
+    if np.iscomplexobj(a):
+        a = a.astype(np.complex128).reshape(-1).view(np.float64)
+    return torch.from_numpy(a.copy()).cuda()
+
+
+def _host_c(t):
+    return t.cpu().numpy().view(np.complex128)
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def _run_sweep(hz, case, pr, precision, nt, m_wh, lam, with_rhs, wh_tol=0.0):
+    import torch
+
+    m = pr.mesh
+    nl = hz.hz_lambda_size(case.pr)
+    assert nl == m.L * 4 * m.NE
+    lin = _dev(lam)
+    lout = torch.full((2 * nl,), float("nan"), dtype=torch.float64, device="cuda")
+    usub = torch.zeros(2 * m.L * m.nly * m.nlx, dtype=torch.float64, device="cuda")
+    rhs = None
+    if with_rhs:
+        rhs = torch.empty(2 * case.n, dtype=torch.float64, device="cuda")
+        hz.hz_rhs(case.pr, rhs)
+    hz.hz_sweep(case.pr, precision, nt, m_wh, wh_tol, lin, lout, rhs, usub)
+    torch.cuda.synchronize()
+    return _host_c(lout).reshape(m.L, 4, m.NE), _host_c(usub).reshape(m.L, m.nly, m.nlx)
+
+
+LAYOUTS = [
+    (8, 8, 4, 4, 2),   # 2x2 subdomains (cross point)
+    (6, 6, 2, 2, 3),   # 3x3 subdomains, P = 3
+    (8, 4, 2, 4, 1),   # 4x1 strips, P = 1
+    (4, 6, 4, 2, 4),   # 1x3 strips, P = 4
+    (6, 4, 3, 2, 5),   # non-square subdomains (NE padding), P = 5
+    (4, 4, 2, 2, 6),   # P = 6
+    (2, 4, 2, 2, 7),   # P = 7, 1x2
+    (3, 3, 3, 3, 3),   # single subdomain
+    (4, 4, 1, 1, 2),   # single-element subdomains
+]
+
+
+@pytest.mark.parametrize("nx,ny,sx,sy,P", LAYOUTS)
+def test_sweep_fp64_matches_oracle(hz, nx, ny, sx, sy, P):
+    wl = _wl(nx, ny, sx, sy, P)
+    case, pr = _pair(hz, wl, g_seed=nx + P)
+    nt = hz.hz_problem_nt(case.pr)
+    assert nt == pr.choose_nt()
+    lam = _rand_lam(pr, 1)
+    got_l, got_u = _run_sweep(hz, case, pr, hz.HZ_FP64, nt, 2, lam, True)
+    ref_l, ref_u, _ = pr.sweep(lam, pr.rhs(), nt, 2, want_u=True)
+    assert _rel(got_u, ref_u) < 1e-12
+    assert _rel(got_l, ref_l) < 1e-12
+    # homogeneous sweep (the GMRES matvec)
+    got_h, _ = _run_sweep(hz, case, pr, hz.HZ_FP64, nt, 2, lam, False)
+    assert _rel(got_h, pr.sweep(lam, None, nt, 2)) < 1e-12
+    case.close()
+
+
+@pytest.mark.parametrize("nx,ny,sx,sy,P", LAYOUTS[:5])
+def test_sweep_fp32_within_bound(hz, nx, ny, sx, sy, P):
+    wl = _wl(nx, ny, sx, sy, P)
+    case, pr = _pair(hz, wl)
+    nt = hz.hz_problem_nt(case.pr)
+    lam = _rand_lam(pr, 2)
+    got_l, got_u = _run_sweep(hz, case, pr, hz.HZ_FP32_REFINE, nt, 5, lam, True)
+    ref_l, ref_u, _ = pr.sweep(lam, pr.rhs(), nt, 5, want_u=True)
+    eu, el = _rel(got_u, ref_u), _rel(got_l, ref_l)
+    print(f"fp32 sweep rel err u {eu:.2e} lambda {el:.2e} (Nt={nt})")
+    assert eu < 2e-4 and el < 2e-4
+
+
+def test_sweep_waveholtz_tolerance_mode(hz):
+    wl = _wl(8, 8, 4, 4, 2, omega=6.0)
+    case, pr = _pair(hz, wl, g_seed=3)
+    nt = hz.hz_problem_nt(case.pr)
+    lam = _rand_lam(pr, 3)
+    got_l, got_u = _run_sweep(hz, case, pr, hz.HZ_FP64, nt, 40, lam, True, wh_tol=1e-6)
+    ref_l, ref_u, iters = pr.sweep(lam, pr.rhs(), nt, 40, wh_tol=1e-6, want_u=True)
+    assert iters.max() < 40  # the tolerance, not the cap, stopped every subdomain
+    assert _rel(got_u, ref_u) < 1e-11
+    assert _rel(got_l, ref_l) < 1e-11
+
+
+def test_sweep_is_deterministic(hz):
+    wl = _wl(8, 8, 4, 4, 3)
+    case, pr = _pair(hz, wl)
+    nt = hz.hz_problem_nt(case.pr)
+    lam = _rand_lam(pr, 4)
+    a, ua = _run_sweep(hz, case, pr, hz.HZ_FP32_REFINE, nt, 3, lam, True)
+    b, ub = _run_sweep(hz, case, pr, hz.HZ_FP32_REFINE, nt, 3, lam, True)
+    assert np.array_equal(a, b) and np.array_equal(ua, ub)
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 4, 5, 6, 7])
+def test_rhs_residual_assembly_match_oracle(hz, P):
+    import torch
+
+    wl = _wl(6, 4, 3, 2, P, box=(-0.5, 1.5, 0.25, 1.0))
+    case, pr = _pair(hz, wl, g_seed=P)
+    b = torch.empty(2 * case.n, dtype=torch.float64, device="cuda")
+    hz.hz_rhs(case.pr, b)
+    ref_b = pr.rhs().ravel()
+    assert _rel(_host_c(b), ref_b) < 1e-14
+    rng = np.random.default_rng(P)
+    u = rng.standard_normal(case.n) + 1j * rng.standard_normal(case.n)
+    r = torch.empty(2 * case.n, dtype=torch.float64, device="cuda")
+    nrm = torch.empty(2, dtype=torch.float64, device="cuda")
+    hz.hz_residual(case.pr, b, _dev(u), r, nrm)
+    ref_r = ref_b - pr.apply_K(u.reshape(pr.c.shape)).ravel()
+    assert _rel(_host_c(r), ref_r) < 1e-12
+    n2 = nrm.cpu().numpy()
+    assert abs(n2[0] - np.sum(np.abs(ref_r) ** 2)) < 1e-10 * n2[0]
+    assert abs(n2[1] - np.sum(np.abs(ref_b) ** 2)) < 1e-12 * n2[1]
+    # assembly of subdomain copies
+    m = pr.mesh
+    us = rng.standard_normal((m.L, m.nly, m.nlx)) + 1j * rng.standard_normal((m.L, m.nly, m.nlx))
+    acc = torch.zeros(2 * case.n, dtype=torch.float64, device="cuda")
+    hz.hz_assemble_add(case.pr, _dev(us), acc)
+    assert _rel(_host_c(acc), pr.assemble_u(us).ravel()) < 1e-14
+
+
+def test_solve_fp64_matches_direct_solve(hz):
+    wl = configs.scaled(configs.config1(), 16, 16, 4, 4, name="cfg1_16x16")
+    case, pr = _pair(hz, wl)
+    opts = hz.hz_default_opts(tol=1e-12, inner_tol=1e-10)
+    st, u, rep = hz.hz_solve(case.pr, opts, n=case.n)
+    assert st == hz.HZ_OK, rep
+    ud = pr.direct_solve().ravel()
+    err = np.linalg.norm(u - ud) / np.linalg.norm(ud)
+    print("fp64 solve", rep, "err vs direct", err)
+    assert rep["rel_residual"] <= 1e-12 and err < 1e-10
+    m = pr.mesh
+    assert rep["wh_iters_max"] == opts.wh_iters
+    assert rep["dof_updates"] == rep["sweeps"] * m.L * m.nlx * m.nly * (rep["nt"] - 1) * opts.wh_iters
+
+
+def test_solve_fp64_iterates_match_oracle(hz):
+    """Same algorithm, fixed budget: g sweep + k GMRES steps + closing sweep,
+    no restart; the DD iterate equals the oracle's to rounding."""
+    wl = _wl(8, 8, 2, 2, 2, omega=8.0)
+    case, pr = _pair(hz, wl, g_seed=5)
+    k = 12
+    opts = hz.hz_default_opts(tol=0.0, inner_tol=0.0, max_refine=1, max_sweeps=k + 2, gmres_restart=50,
+                              wh_iters=4)
+    st, u, rep = hz.hz_solve(case.pr, opts, n=case.n)
+    assert st == hz.HZ_ERR_NOT_CONVERGED and rep["sweeps"] == k + 2 and rep["gmres_iters"] == k
+    nt = pr.choose_nt()
+    ue, info = pr.dd_solve(pr.rhs(), Nt=nt, m_wh=4, outer="gmres", restart=50, tol=0.0, max_sweeps=k + 2)
+    assert info["sweeps"] == k + 2
+    assert np.linalg.norm(u - ue.ravel()) / np.linalg.norm(ue) < 1e-10
+    # plain fixed-point iteration, same budget
+    optp = hz.hz_default_opts(tol=0.0, inner_tol=0.0, max_refine=1, max_sweeps=k + 2, outer=hz.HZ_OUTER_PLAIN,
+                              wh_iters=4)
+    st, up, rep = hz.hz_solve(case.pr, optp, n=case.n)
+    uo, info = pr.dd_solve(pr.rhs(), Nt=nt, m_wh=4, outer="plain", tol=0.0, max_sweeps=k + 2)
+    assert rep["sweeps"] == info["sweeps"] == k + 2
+    assert np.linalg.norm(up - uo.ravel()) / np.linalg.norm(uo) < 1e-10
+
+
+def test_solve_real_gmres_iterates_match_oracle(hz):
+    wl = _wl(8, 8, 4, 4, 2, omega=7.0)
+    case, pr = _pair(hz, wl)
+    k = 10
+    opts = hz.hz_default_opts(tol=0.0, inner_tol=0.0, max_refine=1, max_sweeps=k + 2, gmres_restart=50,
+                              wh_iters=3, outer=hz.HZ_OUTER_RGMRES)
+    st, u, rep = hz.hz_solve(case.pr, opts, n=case.n)
+    ue, info = pr.dd_solve(pr.rhs(), Nt=pr.choose_nt(), m_wh=3, outer="rgmres", restart=50, tol=0.0,
+                           max_sweeps=k + 2)
+    assert np.linalg.norm(u - ue.ravel()) / np.linalg.norm(ue) < 1e-10
+
+
+def test_solve_fp32_refine_reaches_tolerance(hz):
+    wl = configs.scaled(configs.config1(), 16, 16, 4, 4, name="cfg1_16x16")
+    case, pr = _pair(hz, wl)
+    opts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=1e-8, inner_tol=1e-5)
+    st, u, rep = hz.hz_solve(case.pr, opts, n=case.n)
+    ud = pr.direct_solve().ravel()
+    err = np.linalg.norm(u - ud) / np.linalg.norm(ud)
+    print("fp32+refine", rep, "err vs direct", err)
+    assert st == hz.HZ_OK and rep["rel_residual"] <= 1e-8 and err < 1e-6
+
+
+def test_time_step_beyond_cfl_reports_divergence(hz):
+    wl = _wl(8, 8, 4, 4, 3, omega=2.0)
+    case, pr = _pair(hz, wl)
+    opts = hz.hz_default_opts(nt_override=3, max_sweeps=20)
+    with pytest.raises(hz.HzError) as e:
+        hz.hz_solve(case.pr, opts, n=case.n)
+    assert e.value.status == hz.HZ_ERR_DIVERGED
+
+
+def test_zero_source_gives_zero_solution(hz):
+    wl = _wl(4, 4, 2, 2, 2)
+    from paper_2606_21695_gb300.api import Case
+
+    case = Case(wl)
+    hz.hz_problem_set(case.pr, hz.HZ_SOURCE, np.zeros(case.n, complex))
+    st, u, rep = hz.hz_solve(case.pr, hz.hz_default_opts(), n=case.n)
+    assert st == hz.HZ_OK and np.all(u == 0) and rep["sweeps"] == 0
+
+
+def test_invalid_fields_rejected(hz):
+    from paper_2606_21695_gb300.api import Case
+
+    case = Case(_wl(4, 4, 2, 2, 2))
+    bad = np.ones(case.n)
+    bad[3] = -1.0
+    with pytest.raises(hz.HzError):
+        hz.hz_problem_set(case.pr, hz.HZ_WAVE_SPEED, bad)
+    bad[3] = np.nan
+    with pytest.raises(hz.HzError):
+        hz.hz_problem_set(case.pr, hz.HZ_WAVE_SPEED, bad)
+    with pytest.raises(hz.HzError):
+        hz.hz_problem_set(case.pr, hz.HZ_WAVE_SPEED, np.ones(case.n - 1))
+    with pytest.raises(hz.HzError):
+        hz.hz_problem_set(case.pr, hz.HZ_OMEGA, np.array([0.0]))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_config2_full_size_sampled_sweep(hz, precision):
+    """256x256 elements, P=3, 32x32 subdomains (the benchmark workload), one
+    sweep in the benchmark's launch configuration; the oracle recomputes
+    sampled subdomains (each subdomain's cycle depends only on its own data
+    and incoming lambda)."""
+    wl = configs.config2()
+    case, pr = _pair(hz, wl)
+    nt = hz.hz_problem_nt(case.pr)
+    assert nt == pr.choose_nt()
+    lam = _rand_lam(pr, 7) * 1e-2
+    prec = hz.HZ_FP64 if precision == "fp64" else hz.HZ_FP32_REFINE
+    got_l, got_u = _run_sweep(hz, case, pr, prec, nt, 5, lam, True)
+    m = pr.mesh
+    sample = [0, m.Sx - 1, 17 * m.Sx + 9, m.L - m.Sx, m.L - 1, 511]
+    ref_l, ref_u, _ = pr.sweep(lam, pr.rhs(), nt, 5, want_u=True, subset=sample)
+    tol = 1e-12 if precision == "fp64" else 2e-4
+    scale = max(np.max(np.abs(ref_u[sample])), 1e-300)
+    for l in sample:
+        assert np.max(np.abs(got_u[l] - ref_u[l])) < tol * scale, l
+        for e in range(4):
+            r = pr.nbr[l, e]
+            if r >= 0:
+                o = dd.OPPOSITE[e]
+                sl = np.max(np.abs(ref_l[r, o])) + 1e-300
+                assert np.max(np.abs(got_l[r, o] - ref_l[r, o])) < tol * max(sl, np.max(np.abs(lam))), (l, e)
+            else:
+                assert np.all(got_l[l, e] == 0)
