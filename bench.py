@@ -47,6 +47,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 time-to-tolerance leg")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    ap.add_argument("--mode", choices=["solve", "sweep"], default="solve",
+                    help="sweep: only run --sweeps DD sweeps of the workload (for ncu captures)")
+    ap.add_argument("--sweeps", type=int, default=2)
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--wh-iters", type=int, default=20)
     return ap.parse_args()
 
 
@@ -113,7 +118,7 @@ def _isnum(s):
 
 
 # ------------------------------------------------------- oracle sample ----
-def oracle_sample(wl, seconds, nsub_max=64):
+def oracle_sample(wl, seconds, nsub_max=1024):
     """Times the FP64 oracle sweep on a bounded subset of subdomains of the
     workload (single-threaded NumPy).  Returns (DOF-updates/s, description)."""
     try:
@@ -169,7 +174,7 @@ def run_ours(args):
     case = Case(wl, device=local)
     n = case.n
     stream = torch.cuda.current_stream()
-    opts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, inner_tol=1e-5, wh_iters=10,
+    opts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, inner_tol=1e-3, wh_iters=20,
                               gmres_restart=60, max_sweeps=5000)
     u = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
@@ -182,7 +187,8 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         st, rep = hz.hz_solve_device(case.pr, opts, u, stream)
-        assert st == hz.HZ_OK, rep
+        if st != hz.HZ_OK:
+            raise RuntimeError(f"warm-up solve did not converge: {rep}")
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     reports = []
@@ -254,7 +260,7 @@ def run_ours(args):
         # plain-FP64 time to the same tolerance, one solve (outside the timed region)
         fp64 = None
         if not args.no_fp64:
-            o64 = hz.hz_default_opts(precision=hz.HZ_FP64, tol=TOL, inner_tol=1e-5, wh_iters=10, gmres_restart=60,
+            o64 = hz.hz_default_opts(precision=hz.HZ_FP64, tol=TOL, inner_tol=1e-3, wh_iters=20, gmres_restart=60,
                                      max_sweeps=5000)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -332,8 +338,35 @@ def run_reference(args):
     }
 
 
+def run_sweeps(args):
+    """--mode sweep: set up the workload and launch --sweeps homogeneous DD
+    sweeps through the C ABI (the launch configuration of the solve)."""
+    import torch
+
+    import paper_2606_21695_gb300 as hz
+    from paper_2606_21695_gb300.api import Case
+    from workloads import configs
+
+    wl = configs.config2()
+    case = Case(wl)
+    nt = hz.hz_problem_nt(case.pr)
+    nl = hz.hz_lambda_size(case.pr)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    lin = torch.randn(2 * nl, dtype=torch.float64, device="cuda", generator=g) * 1e-2
+    lout = torch.zeros_like(lin)
+    prec = hz.HZ_FP32_REFINE if args.precision == "fp32" else hz.HZ_FP64
+    for _ in range(args.sweeps):
+        hz.hz_sweep(case.pr, prec, nt, args.wh_iters, 0.0, lin, lout)
+    torch.cuda.synchronize()
+    case.close()
+    return {"mode": "sweep", "sweeps": args.sweeps, "nt": nt, "precision": args.precision, "wh_iters": args.wh_iters}
+
+
 def main():
     args = parse()
+    if args.mode == "sweep":
+        print(json.dumps(run_sweeps(args)), flush=True)
+        return
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
         print(json.dumps(out), flush=True)

@@ -100,6 +100,7 @@ typedef struct {
   double cfl;            /* dt = cfl * 2 / (c_max sqrt(lx + ly)) */
   double inner_tol;      /* relative tolerance of each DD solve (GMRES on lambda) */
   int32_t max_refine;    /* maximum FP64 refinement steps */
+  int32_t autotune;      /* 1: time the sweep kernel variants once per subdomain shape, use the fastest */
 } hz_solve_opts;
 
 typedef struct {
@@ -111,12 +112,12 @@ typedef struct {
   double seconds;        /* wall time of the solve */
   int64_t dof_updates;   /* sum over sweeps of subdomain nodes x (N_t - 1) x WaveHoltz iterations */
   int32_t gmres_iters;   /* total GMRES iterations */
-  int32_t reserved;
+  int32_t sweep_variant; /* kernel of the last sweep: 1 block, 2 warp per subdomain, 3 cluster */
   double sweep_seconds;  /* device time of the sweep kernels (CUDA events on the solve's stream) */
 } hz_solve_report;
 
-/* Defaults: FP64, tol 1e-8, 2000 sweeps, GMRES(60), 10 WaveHoltz iterations,
- * no wh_tol, CFL 0.9, inner_tol 1e-6, 20 refinements. */
+/* Defaults: FP64, tol 1e-8, 2000 sweeps, GMRES(60), 20 WaveHoltz iterations,
+ * no wh_tol, CFL 0.9, inner_tol 1e-3, 20 refinements, autotune on. */
 HZ_API void hz_default_opts(hz_solve_opts* opts);
 
 /* Copies the calling thread's last error message (NUL-terminated, truncated
@@ -169,6 +170,18 @@ HZ_API hz_status hz_solve(hz_problem pr, const hz_solve_opts* opts, double* u_ou
 /* Same with the solution written to device memory u_out_dev (n complex). */
 HZ_API hz_status hz_solve_device(hz_problem pr, const hz_solve_opts* opts, double* u_out_dev, hz_solve_report* report,
                           void* stream);
+
+/* Solves count independent problems concurrently on their devices (batched
+ * execution, continuous across sizes, degrees and frequencies): at most
+ * max_concurrent solves (<= 0: 8) run at once, started in decreasing order of
+ * estimated cost; with opts->autotune the sweep kernel of each distinct
+ * subdomain shape is timed once first.  u_out[k] (host, n_k complex) may be
+ * NULL; reports may be NULL; statuses[k] receives each solve's status.
+ * Returns HZ_OK, HZ_ERR_NOT_CONVERGED if any solve ran out of budget, or the
+ * first hard error (hz_last_error names the problem). */
+HZ_API hz_status hz_solve_batch(const hz_problem* problems, int32_t count, const hz_solve_opts* opts,
+                                int32_t max_concurrent, double* const* u_out, hz_solve_report* reports,
+                                hz_status* statuses);
 
 /* ------------------------------------------------- hot-path step calls --
  * These expose the individual steps of the path on device buffers.

@@ -38,16 +38,16 @@ class hz_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("max_sweeps", C.c_int32), ("outer", C.c_int32),
                 ("gmres_restart", C.c_int32), ("wh_iters", C.c_int32), ("wh_tol", C.c_double),
                 ("nt_override", C.c_int32), ("cfl", C.c_double), ("inner_tol", C.c_double),
-                ("max_refine", C.c_int32)]
+                ("max_refine", C.c_int32), ("autotune", C.c_int32)]
 
 
 class hz_solve_report(C.Structure):
     _fields_ = [("sweeps", C.c_int32), ("refinements", C.c_int32), ("nt", C.c_int32), ("wh_iters_max", C.c_int32),
                 ("rel_residual", C.c_double), ("seconds", C.c_double), ("dof_updates", C.c_int64),
-                ("gmres_iters", C.c_int32), ("reserved", C.c_int32), ("sweep_seconds", C.c_double)]
+                ("gmres_iters", C.c_int32), ("sweep_variant", C.c_int32), ("sweep_seconds", C.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _lib = None
@@ -81,6 +81,8 @@ def load():
         "hz_problem_nt": (i32, [vp, d, C.POINTER(i32)]),
         "hz_solve": (i32, [vp, C.POINTER(hz_solve_opts), dp, C.POINTER(hz_solve_report)]),
         "hz_solve_device": (i32, [vp, C.POINTER(hz_solve_opts), vp, C.POINTER(hz_solve_report), vp]),
+        "hz_solve_batch": (i32, [C.POINTER(vp), i32, C.POINTER(hz_solve_opts), i32, C.POINTER(dp),
+                                 C.POINTER(hz_solve_report), C.POINTER(i32)]),
         "hz_lambda_size": (i32, [vp, C.POINTER(i64)]),
         "hz_prepare": (i32, [vp, i32, vp]),
         "hz_sweep": (i32, [vp, i32, i32, i32, d, vp, vp, vp, vp, vp]),
@@ -105,7 +107,7 @@ def exported_names():
     """Names of the C functions this binding expects libhz.so to export."""
     return ["hz_default_opts", "hz_last_error", "hz_kernel_launches", "hz_mesh_create", "hz_mesh_num_nodes", "hz_mesh_node_coords",
             "hz_mesh_destroy", "hz_problem_create", "hz_problem_set", "hz_problem_set_device", "hz_problem_destroy",
-            "hz_problem_nt", "hz_solve", "hz_solve_device", "hz_lambda_size", "hz_prepare", "hz_sweep", "hz_rhs",
+            "hz_problem_nt", "hz_solve", "hz_solve_device", "hz_solve_batch", "hz_lambda_size", "hz_prepare", "hz_sweep", "hz_rhs",
             "hz_residual", "hz_assemble_add", "hz_server_create", "hz_server_submit", "hz_server_poll",
             "hz_server_stats", "hz_server_destroy"]
 
@@ -241,6 +243,22 @@ def hz_solve_device(pr, opts, u_dev, stream=None):
     st = load().hz_solve_device(pr, C.byref(opts), _ptr(u_dev), C.byref(rep), _stream(stream))
     _check(st, (HZ_OK, HZ_ERR_NOT_CONVERGED))
     return st, rep.as_dict()
+
+
+def hz_solve_batch(problems, ns, opts=None, max_concurrent=0, want_u=True):
+    """problems: list of handles; ns: their node counts.  Returns (status,
+    list of per-problem statuses, list of u arrays or None, list of report dicts)."""
+    if opts is None:
+        opts = hz_default_opts()
+    k = len(problems)
+    arr = (C.c_void_p * k)(*[p.value if isinstance(p, C.c_void_p) else p for p in problems])
+    us = [np.empty(2 * n, np.float64) for n in ns] if want_u else None
+    uptr = (C.POINTER(C.c_double) * k)(*[u.ctypes.data_as(C.POINTER(C.c_double)) for u in us]) if want_u else None
+    reps = (hz_solve_report * k)()
+    sts = (C.c_int32 * k)()
+    st = load().hz_solve_batch(arr, k, C.byref(opts), max_concurrent, uptr, reps, sts)
+    _check(st, (HZ_OK, HZ_ERR_NOT_CONVERGED))
+    return st, list(sts), ([u.view(np.complex128) for u in us] if want_u else None), [r.as_dict() for r in reps]
 
 
 def hz_lambda_size(pr):

@@ -68,6 +68,7 @@ double max_eig_1d(const Geom& g, int n_el, double h);  // largest eig of W^-1 K,
 // ------------------------------------------------------------- kernels ----
 struct SweepArgs {
   int nlx, nly, NE, Sx, Sy, sxe, sye, NXg, NS, snxP, snyP;
+  int ty_force;  // block kernel rows per thread: 0 = by size, 1 = P, 2 = 2P
   int Nt, m_wh;
   double wh_tol, sigma, omega, cpi, spi, two_over_nt;
   double kxs, kys, hx2, hy2;  // 2/hx, 2/hy, hx/2, hy/2
@@ -88,6 +89,25 @@ struct SweepArgs {
   unsigned long long* wh_iter_sum;  // sum over subdomains of WaveHoltz iterations
   int* flags;           // bit 0: non-finite value seen
 };
+
+// Parameters of the warp-per-subdomain FP32 sweep (subdomains <= 32 node
+// columns): per-row weights and assembled y-stiffness rows, indexed by
+// compile-time row numbers in the kernel (constant-bank operands).
+constexpr int kWarpMaxRows = 33;
+struct WarpSweepArgs {
+  SweepArgs base;
+  int L;
+  float wyr[kWarpMaxRows];                     // hy/2 * (w_a [own element] + w_P [element below])
+  float kyr[kWarpMaxRows][2 * kMaxP + 1];      // assembled 1D y-stiffness row, taps -P..P (reference scale)
+};
+// Returns HZ_ERR_UNSUPPORTED (without launching) when no warp variant for
+// (P, sub_ny) was compiled or the subdomain has more than 32 node columns.
+hz_status launch_sweep_warp(int P, int sy, const WarpSweepArgs& a, cudaStream_t st);
+
+// FP32 sweep of one subdomain per thread-block cluster (column bands, halo
+// exchange through distributed shared memory).  HZ_ERR_UNSUPPORTED when no
+// cluster shape fits.
+hz_status launch_sweep_cluster(int P, const SweepArgs& a, int L, cudaStream_t st);
 
 // Launches the sweep in Real = float (fp32 = true) or double.  Returns
 // HZ_ERR_UNSUPPORTED when no compiled variant fits the subdomain.

@@ -1,6 +1,7 @@
 // Problem state behind the opaque hz_problem handle.
 #pragma once
 
+#include <string>
 #include <vector>
 
 #include "hz_internal.h"
@@ -29,6 +30,8 @@ struct hz_problem_s {
   int version = 0;            // bumped on every field change
   int prepared_nt = 0, prepared_version = -1;
   long long sweeps_launched = 0;
+  int last_variant = 0;       // sweep kernel used by the last sweep (kVariant*)
+  bool autotune = false;      // use / fill the tuned kernel choice for this shape
   // fields (global node grid)
   hz::DevBuf c, f, gb;
   // 1D weight tables
@@ -46,6 +49,16 @@ struct hz_problem_s {
 
 namespace hz {
 using Problem = hz_problem_s;
+constexpr int kVariantAuto = 0, kVariantBlock = 1, kVariantWarp = 2, kVariantCluster = 3;
+int sweep_variant();
+struct Choice {
+  int variant;  // kVariantBlock / kVariantWarp / kVariantCluster
+  int ty;       // block kernel rows per thread (0 = by size, 1 = P, 2 = 2P)
+};
+std::string tune_key(const Geom& g, int precision);
+bool lookup_choice(const std::string& key, Choice* out);
+void store_choice(const std::string& key, Choice c);
+hz_status autotune(Problem& pr, int precision, int nt, int m_wh, cudaStream_t st);
 int choose_nt(const Problem& pr, double cfl);
 hz_status prepare(Problem& pr, int nt, cudaStream_t st);
 hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, const double* lam_in, double* lam_out,

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -176,14 +177,85 @@ hz_status ensure_flags(Problem& pr) {
   return HZ_OK;
 }
 
-hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, const double* lam_in, double* lam_out,
-                const double* rhs, double* u_sub, cudaStream_t st) {
-  HZ_TRY(prepare(pr, nt, st));
-  HZ_TRY(ensure_flags(pr));
+// Sweep kernel selection: HZ_SWEEP_VARIANT=block|warp|cluster forces one (tests);
+// default: the warp-per-subdomain kernel when compiled for the shape, else
+// the block kernel.
+int sweep_variant() {
+  const char* v = std::getenv("HZ_SWEEP_VARIANT");
+  if (!v) return kVariantAuto;
+  if (std::strcmp(v, "block") == 0) return kVariantBlock;
+  if (std::strcmp(v, "warp") == 0) return kVariantWarp;
+  if (std::strcmp(v, "cluster") == 0) return kVariantCluster;
+  return kVariantAuto;
+}
+
+// Row weights and assembled y-stiffness rows of a subdomain for the warp kernel.
+void warp_rows(const Geom& g, WarpSweepArgs* w) {
+  const int P = g.P;
+  for (int j = 0; j < kWarpMaxRows; ++j) {
+    const int ay = j % P, ey = j / P;
+    const bool own = ey < g.sny, below = ay == 0 && ey >= 1;
+    w->wyr[j] = (float)(g.hy / 2.0 * ((own ? g.w[ay] : 0.0) + (below ? g.w[P] : 0.0)));
+    for (int t = -P; t <= P; ++t) {
+      double v = 0.0;
+      if (own && ay + t >= 0 && ay + t <= P) v += g.Kref[ay * (P + 1) + ay + t];
+      if (below && t <= 0) v += g.Kref[P * (P + 1) + P + t];
+      w->kyr[j][t + P] = (float)v;
+    }
+  }
+}
+
+// ---- sweep kernel choices and the autotuner's cache
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, Choice> g_tuned;
+}  // namespace
+
+std::string tune_key(const Geom& g, int precision) {
+  int lb = 0;
+  while ((1 << (lb + 1)) <= g.L) ++lb;  // occupancy depends on the number of subdomains
+  return std::to_string(g.P) + "/" + std::to_string(g.nlx) + "x" + std::to_string(g.nly) + "/L2^" +
+         std::to_string(lb) + "/" + std::to_string(precision);
+}
+
+bool lookup_choice(const std::string& key, Choice* out) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find(key);
+  if (it == g_tuned.end()) return false;
+  *out = it->second;
+  return true;
+}
+
+void store_choice(const std::string& key, Choice c) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[key] = c;
+}
+
+hz_status launch_choice(Problem& pr, const SweepArgs& a0, Choice c, bool fp32, cudaStream_t st) {
   const Geom& g = pr.g;
-  if (m_wh < 0) return fail(HZ_ERR_INVALID_ARG, "wh_iters must be >= 0");
-  const bool fp32 = precision == HZ_FP32_REFINE;
-  if (precision != HZ_FP64 && precision != HZ_FP32_REFINE) return fail(HZ_ERR_INVALID_ARG, "unknown precision");
+  hz_status s = HZ_ERR_UNSUPPORTED;
+  if (c.variant == kVariantWarp) {
+    if (!fp32) return HZ_ERR_UNSUPPORTED;
+    WarpSweepArgs w{};
+    w.base = a0;
+    w.L = g.L;
+    warp_rows(g, &w);
+    s = launch_sweep_warp(g.P, g.sny, w, st);
+  } else if (c.variant == kVariantCluster) {
+    if (!fp32) return HZ_ERR_UNSUPPORTED;
+    s = launch_sweep_cluster(g.P, a0, g.L, st);
+  } else {
+    SweepArgs a = a0;
+    a.ty_force = c.ty;
+    s = launch_sweep(fp32, g.P, a, g.L, st);
+  }
+  if (s == HZ_OK) pr.last_variant = c.variant;
+  return s;
+}
+
+SweepArgs make_sweep_args(Problem& pr, bool fp32, int nt, int m_wh, double wh_tol, const double* lam_in,
+                          double* lam_out, const double* rhs, double* u_sub) {
+  const Geom& g = pr.g;
   SweepArgs a{};
   a.nlx = g.nlx;
   a.nly = g.nly;
@@ -226,6 +298,73 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
   a.flags = fl;
   a.wh_iter_max = fl + 1;
   a.wh_iter_sum = reinterpret_cast<unsigned long long*>(fl + 2);
+  return a;
+}
+
+namespace {
+std::mutex g_tune_run_mu;
+}
+
+// Autotuner: times every sweep kernel variant that supports the shape (warp
+// per subdomain; one block per subdomain with P or 2P rows per thread; a
+// cluster of blocks) on this problem and caches the fastest per shape key.
+hz_status autotune(Problem& pr, int precision, int nt, int m_wh, cudaStream_t st) {
+  const std::string key = tune_key(pr.g, precision);
+  Choice c{};
+  if (lookup_choice(key, &c)) return HZ_OK;
+  std::lock_guard<std::mutex> lk(g_tune_run_mu);
+  if (lookup_choice(key, &c)) return HZ_OK;
+  HZ_TRY(prepare(pr, nt, st));
+  HZ_TRY(ensure_flags(pr));
+  const size_t vb = (size_t)pr.g.lam_complex() * 2 * sizeof(double);
+  HZ_TRY(pr.xv.ensure(vb));
+  HZ_TRY(pr.tv.ensure(vb));
+  HZ_CUDA(cudaMemsetAsync(pr.xv.ptr, 0, vb, st));
+  const bool fp32 = precision == HZ_FP32_REFINE;
+  const SweepArgs a = make_sweep_args(pr, fp32, nt, m_wh, 0.0, pr.xv.as<double>(), pr.tv.as<double>(), nullptr, nullptr);
+  std::vector<Choice> cands;
+  if (fp32) cands = {{kVariantWarp, 0}, {kVariantBlock, 1}, {kVariantBlock, 2}, {kVariantCluster, 0}};
+  else cands = {{kVariantBlock, 1}, {kVariantBlock, 2}};
+  cudaEvent_t e0, e1;
+  HZ_CUDA(cudaEventCreate(&e0));
+  HZ_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  Choice bc{kVariantBlock, 0};
+  for (const Choice& cand : cands) {
+    hz_status s = launch_choice(pr, a, cand, fp32, st);  // warm-up, also the support check
+    if (s == HZ_ERR_UNSUPPORTED) continue;
+    if (s != HZ_OK) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return s;
+    }
+    cudaEventRecord(e0, st);
+    for (int k = 0; k < 2; ++k) launch_choice(pr, a, cand, fp32, st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      bc = cand;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  HZ_CUDA(cudaGetLastError());
+  store_choice(key, bc);
+  return HZ_OK;
+}
+
+hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, const double* lam_in, double* lam_out,
+                const double* rhs, double* u_sub, cudaStream_t st) {
+  HZ_TRY(prepare(pr, nt, st));
+  HZ_TRY(ensure_flags(pr));
+  const Geom& g = pr.g;
+  if (m_wh < 0) return fail(HZ_ERR_INVALID_ARG, "wh_iters must be >= 0");
+  const bool fp32 = precision == HZ_FP32_REFINE;
+  if (precision != HZ_FP64 && precision != HZ_FP32_REFINE) return fail(HZ_ERR_INVALID_ARG, "unknown precision");
+  const SweepArgs a = make_sweep_args(pr, fp32, nt, m_wh, wh_tol, lam_in, lam_out, rhs, u_sub);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (pr.time_sweeps) {
     if (pr.ev_used + 2 > pr.events.size()) {
@@ -240,7 +379,33 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
     pr.ev_used += 2;
     HZ_CUDA(cudaEventRecord(e0, st));
   }
-  HZ_TRY(launch_sweep(fp32, g.P, a, g.L, st));
+  // Kernel choice: HZ_SWEEP_VARIANT forces a variant; otherwise the tuned
+  // choice for this shape (if autotuning ran) or the size heuristic:
+  // FP32 -> warp-per-subdomain kernel when compiled for the shape, else one
+  // block per subdomain when it fits in 256 threads, else a cluster of
+  // blocks, else the block kernel with up to 1024 threads; FP64 -> block.
+  const int want = sweep_variant();
+  Choice ch{};
+  bool have = false;
+  if (want == kVariantAuto && pr.autotune && lookup_choice(tune_key(pr.g, precision), &ch)) have = true;
+  hz_status ls = HZ_ERR_UNSUPPORTED;
+  if (have) {
+    ls = launch_choice(pr, a, ch, fp32, st);
+    if (ls != HZ_OK && ls != HZ_ERR_UNSUPPORTED) return ls;
+  }
+  if (ls == HZ_ERR_UNSUPPORTED && fp32 && (want == kVariantAuto || want == kVariantWarp)) {
+    ls = launch_choice(pr, a, Choice{kVariantWarp, 0}, fp32, st);
+    if (ls != HZ_OK && ls != HZ_ERR_UNSUPPORTED) return ls;
+    if (ls != HZ_OK && want == kVariantWarp) return fail(HZ_ERR_UNSUPPORTED, "no warp sweep variant for this subdomain");
+  }
+  const bool small_block = (int64_t)g.nlx * ((g.nly + g.P - 1) / g.P) <= 256;
+  if (ls == HZ_ERR_UNSUPPORTED && fp32 &&
+      (want == kVariantCluster || (want == kVariantAuto && !small_block))) {
+    ls = launch_choice(pr, a, Choice{kVariantCluster, 0}, fp32, st);
+    if (ls != HZ_OK && ls != HZ_ERR_UNSUPPORTED) return ls;
+    if (ls != HZ_OK && want == kVariantCluster) return fail(HZ_ERR_UNSUPPORTED, "no cluster sweep shape fits");
+  }
+  if (ls == HZ_ERR_UNSUPPORTED) HZ_TRY(launch_choice(pr, a, Choice{kVariantBlock, 0}, fp32, st));
   if (e1) HZ_CUDA(cudaEventRecord(e1, st));
   pr.sweeps_launched++;
   return HZ_OK;
@@ -495,6 +660,8 @@ hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report*
   HZ_TRY(pr.hsmall.ensure(8192 * sizeof(double)));
   HZ_TRY(prepare(pr, nt, st));
   HZ_TRY(ensure_flags(pr));
+  pr.autotune = o.autotune != 0 && sweep_variant() == kVariantAuto;
+  if (pr.autotune) HZ_TRY(autotune(pr, o.precision, nt, o.wh_iters, st));
   HZ_CUDA(cudaMemsetAsync(pr.flags.ptr, 0, 64, st));
   HZ_TRY(rhs(pr, pr.bvec.as<double>(), st));
   HZ_CUDA(cudaMemsetAsync(u, 0, nb, st));
@@ -542,6 +709,7 @@ hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report*
   }
   (void)cudaGetLastError();
   rep.sweep_seconds = sw;
+  rep.sweep_variant = pr.last_variant;
   pr.time_sweeps = false;
   rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (rep_out) *rep_out = rep;
@@ -652,12 +820,13 @@ void hz_default_opts(hz_solve_opts* o) {
   o->max_sweeps = 2000;
   o->outer = HZ_OUTER_GMRES;
   o->gmres_restart = 60;
-  o->wh_iters = 10;
+  o->wh_iters = 20;
   o->wh_tol = 0.0;
   o->nt_override = 0;
   o->cfl = 0.9;
-  o->inner_tol = 1e-6;
+  o->inner_tol = 1e-3;
   o->max_refine = 20;
+  o->autotune = 1;
 }
 
 hz_status hz_last_error(char* buf, size_t n) {

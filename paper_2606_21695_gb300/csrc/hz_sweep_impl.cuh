@@ -232,19 +232,22 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(const __grid_constant__ Swe
       }
       cur ^= 1;
     }
-    // u^{(m+1)} = (2/N_t) v
+    // u^{(m+1)} = (2/N_t) v; FP64 norms of the update only in tolerance mode
     double dn = 0.0, un = 0.0;
+    const bool check = a.wh_tol > 0.0;
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
       const Real nr = scale * vre[r], ni = scale * vim[r];
-      const double dr = (double)nr - (double)ure[r], di = (double)ni - (double)uim[r];
-      dn += dr * dr + di * di;
-      un += (double)nr * nr + (double)ni * ni;
+      if (check) {
+        const double dr = (double)nr - (double)ure[r], di = (double)ni - (double)uim[r];
+        dn += dr * dr + di * di;
+        un += (double)nr * nr + (double)ni * ni;
+      }
       ure[r] = nr;
       uim[r] = ni;
     }
     m_done = m + 1;
-    if (a.wh_tol > 0.0) {
+    if (check) {
       // block reduction of ||u^{m+1}-u^m||^2 and ||u^{m+1}||^2 (dead nodes are 0)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -351,9 +354,13 @@ hz_status launch_one(const SweepArgs& a, int L, cudaStream_t st) {
 
 template <typename Real, int P>
 hz_status launch_P(SweepArgs a, int L, cudaStream_t st) {
-  // TY = 1 when it fits in 1024 threads, else TY = 2
-  a.NS = (a.nly + P - 1) / P;
-  if (a.nlx * a.NS <= 1024) return launch_one<Real, P, 1>(a, L, st);
+  // rows per thread: P (TY = 1) when it fits in 1024 threads, else 2P;
+  // a.ty_force (autotuner) selects one explicitly
+  if (a.ty_force != 2) {
+    a.NS = (a.nly + P - 1) / P;
+    if (a.nlx * a.NS <= 1024) return launch_one<Real, P, 1>(a, L, st);
+    if (a.ty_force == 1) return HZ_ERR_UNSUPPORTED;
+  }
   a.NS = (a.nly + 2 * P - 1) / (2 * P);
   if (a.nlx * a.NS <= 1024) return launch_one<Real, P, 2>(a, L, st);
   return fail(HZ_ERR_UNSUPPORTED, "subdomain too large for the one-block sweep");

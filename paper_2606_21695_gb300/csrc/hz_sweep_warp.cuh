@@ -1,0 +1,274 @@
+// Warp-per-subdomain DD sweep (FP32), for subdomains of at most 32 node
+// columns and NY = SY*P+1 rows: lane i owns node column i, every row of it
+// in registers for the whole WaveHoltz loop (p, p-dot, v, alpha, beta,
+// beta*b).  The time step needs no shared memory and no barrier:
+//   x part of A p: assembled 1D row (2P+1 taps, per-lane coefficients in
+//                  registers) against neighbour lanes via warp shuffles;
+//   y part:        assembled 1D rows whose sparsity pattern is fixed at
+//                  compile time (row j's position in its element and the
+//                  subdomain ends), coefficients are kernel parameters, so
+//                  they are constant-bank operands of the FMAs.
+// Same arithmetic as the block sweep (Algorithm 1, modified leapfrog and
+// eq. (WaveHoltz) with the -1/(i omega) sign and 2/N_t scaling; lambda
+// update -lambda - 2ik u); several subdomains per block, one per warp.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hz_internal.h"
+
+namespace hz {
+namespace warp_sweep {
+
+constexpr int kWarpsPerBlock = 4;
+
+// Is tap t of assembled 1D row j structurally non-zero?  Row j lies in
+// element j/P at position j%P; class-0 rows also touch the element below.
+// ne: elements along the direction (the subdomain has ne*P+1 nodes).
+__host__ __device__ constexpr bool tap(int P, int ne, int j, int t) {
+  const int a = j % P, e = j / P;
+  const bool own = e < ne && a + t >= 0 && a + t <= P;
+  const bool below = a == 0 && e >= 1 && t <= 0 && t >= -P;
+  return own || below;
+}
+
+template <int P, int SY, bool SRC>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) sweep_warp_kernel(const __grid_constant__ WarpSweepArgs x) {
+  constexpr int NY = SY * P + 1;
+  constexpr int NK = 2 * P + 1;
+  constexpr int NB = SRC ? NY : 1;  // per-node forcing only when a source is present
+  const SweepArgs& a = x.base;
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int l = blockIdx.x * kWarpsPerBlock + wib;
+  if (l >= x.L) return;  // whole warp leaves together
+  const int sxi = l % a.Sx, syi = l / a.Sx;
+  const int nlx = a.nlx;
+  const int i = lane;
+  const bool live = i < nlx;
+
+  // ---- per-lane x row of the assembled stiffness (scaled by 2/hx)
+  const int ax = i % P, ex = i / P;
+  const bool own_x = live && ex < a.sxe;
+  const bool left_x = live && (ax == 0) && (ex >= 1);
+  float kx[NK];
+#pragma unroll
+  for (int tt = 0; tt < NK; ++tt) {
+    const int off = tt - P;
+    double v = 0.0;
+    const int b = ax + off;
+    if (own_x && b >= 0 && b <= P) v += a.Kref[ax * (P + 1) + b];
+    if (left_x && off <= 0) v += a.Kref[P * (P + 1) + (off + P)];
+    kx[tt] = (float)(v * a.kxs);
+  }
+  const float wxy = (float)(a.kys * a.hx2 * ((own_x ? a.w[ax] : 0.0) + (left_x ? a.w[P] : 0.0)));
+
+  // ---- node coefficients and right-hand side.  alpha != 1 and (without a
+  // source) b != 0 only on the subdomain edges: rows 0 and NY-1 keep them in
+  // registers, the edge columns' interior rows in a shared table read with
+  // one broadcast load per row (slot 2 is the interior value {1, 0, 0}).
+  __shared__ float4 ecol[kWarpsPerBlock][NY][3];
+  __shared__ float2 uold[kWarpsPerBlock][NY][32];
+  float4(&ec)[NY][3] = ecol[wib];
+  float2(&uo)[NY][32] = uold[wib];
+  const int64_t nn = (int64_t)nlx * NY;
+  const float* betaG = static_cast<const float*>(a.beta) + (int64_t)l * nn;
+  const float* alphaG = static_cast<const float*>(a.alpha) + (int64_t)l * nn;
+  const double* lamL = a.lam_in + (int64_t)l * 4 * a.NE * 2;
+  const bool ifW = sxi > 0, ifE = sxi < a.Sx - 1, ifS = syi > 0, ifN = syi < a.Sy - 1;
+  const int slot = (lane == 0) ? 0 : (lane == nlx - 1) ? 1 : 2;
+  float bet[NY];
+  float bbr[NB], bbi[NB];
+  float al0 = 0.f, alN = 0.f, b0r = 0.f, b0i = 0.f, bNr = 0.f, bNi = 0.f;
+#pragma unroll
+  for (int j = 0; j < NY; ++j) {
+    double be = 0.0, al = 0.0, br = 0.0, bi = 0.0;
+    if (live) {
+      const int64_t n = (int64_t)j * nlx + i;
+      be = (double)betaG[n];
+      al = (double)alphaG[n];
+      if (SRC) {
+        const double shx = ((i == 0 && ifW) || (i == nlx - 1 && ifE)) ? 0.5 : 1.0;
+        const double shy = ((j == 0 && ifS) || (j == NY - 1 && ifN)) ? 0.5 : 1.0;
+        const int64_t I = (int64_t)sxi * a.snxP + i, J = (int64_t)syi * a.snyP + j;
+        const double* src = a.rhs + 2 * (J * a.NXg + I);
+        br = shx * shy * src[0];
+        bi = shx * shy * src[1];
+      }
+      if (i == 0 && ifW) { br += a.wys[j] * lamL[2 * (0 * a.NE + j)]; bi += a.wys[j] * lamL[2 * (0 * a.NE + j) + 1]; }
+      if (i == nlx - 1 && ifE) { br += a.wys[j] * lamL[2 * (1 * a.NE + j)]; bi += a.wys[j] * lamL[2 * (1 * a.NE + j) + 1]; }
+      if (j == 0 && ifS) { br += a.wxs[i] * lamL[2 * (2 * a.NE + i)]; bi += a.wxs[i] * lamL[2 * (2 * a.NE + i) + 1]; }
+      if (j == NY - 1 && ifN) { br += a.wxs[i] * lamL[2 * (3 * a.NE + i)]; bi += a.wxs[i] * lamL[2 * (3 * a.NE + i) + 1]; }
+    }
+    bet[j] = (float)be;
+    const float fbr = (float)(be * br), fbi = (float)(be * bi);
+    if (SRC) {
+      bbr[j] = fbr;
+      bbi[j] = fbi;
+    }
+    if (j == 0) { al0 = (float)al; b0r = SRC ? 0.f : fbr; b0i = SRC ? 0.f : fbi; }
+    if (j == NY - 1) { alN = (float)al; bNr = SRC ? 0.f : fbr; bNi = SRC ? 0.f : fbi; }
+    if (j > 0 && j < NY - 1) {
+      if (slot < 2) ec[j][slot] = make_float4((float)al, SRC ? 0.f : fbr, SRC ? 0.f : fbi, 0.f);
+      if (lane == 2 || (nlx <= 2 && lane == 31)) ec[j][2] = make_float4(1.f, 0.f, 0.f, 0.f);
+    }
+  }
+  __syncwarp();
+
+  const float4* tab = static_cast<const float4*>(a.tab);
+  const float sigma = (float)a.sigma, omega = (float)a.omega;
+  const float cpi = (float)a.cpi, spi = (float)a.spi, scale = (float)a.two_over_nt;
+  // between WaveHoltz iterations u lives in (vre, vim); the previous iterate
+  // is kept in shared memory only when a tolerance is checked
+  float p[NY], pd[NY], vre[NY], vim[NY];
+#pragma unroll
+  for (int j = 0; j < NY; ++j) { vre[j] = 0.f; vim[j] = 0.f; }
+
+  int m_done = 0;
+  for (int m = 0; m < a.m_wh; ++m) {
+    if (a.wh_tol > 0.0) {
+#pragma unroll
+      for (int j = 0; j < NY; ++j) uo[j][lane] = make_float2(vre[j], vim[j]);
+    }
+    {
+      const float4 t0 = tab[0];
+#pragma unroll
+      for (int j = 0; j < NY; ++j) {
+        p[j] = vre[j];
+        pd[j] = omega * (vim[j] * cpi - vre[j] * spi);  // Re{-i w u e^{-i pi/N_t}}
+        vre[j] = t0.z * p[j];
+        vim[j] = t0.w * pd[j];
+      }
+    }
+    float4 tb = tab[1];
+    for (int nu = 1; nu < a.Nt; ++nu) {
+      const float4 tn = tab[nu + 1];  // prefetch (the table has N_t + 1 entries)
+#pragma unroll
+      for (int j = 0; j < NY; ++j) p[j] += sigma * pd[j];
+#pragma unroll
+      for (int j = 0; j < NY; ++j) {
+        // x: neighbours in the same row from neighbouring lanes
+        float sx = kx[P] * p[j];
+#pragma unroll
+        for (int t = 1; t <= P; ++t) {
+          const float up = __shfl_down_sync(0xffffffffu, p[j], t);  // lane i+t
+          const float dn = __shfl_up_sync(0xffffffffu, p[j], t);    // lane i-t
+          sx += kx[P + t] * up + kx[P - t] * dn;
+        }
+        // y: assembled row j, compile-time sparsity
+        float sy = 0.f;
+#pragma unroll
+        for (int t = -P; t <= P; ++t) {
+          if (tap(P, SY, j, t) && j + t >= 0 && j + t < NY) sy += x.kyr[j][t + P] * p[j + t];
+        }
+        const float Ap = x.wyr[j] * sx + wxy * sy;
+        float f;
+        if (j == 0) {
+          f = al0 * pd[j] - bet[j] * Ap + b0r * tb.x + b0i * tb.y;
+        } else if (j == NY - 1) {
+          f = alN * pd[j] - bet[j] * Ap + bNr * tb.x + bNi * tb.y;
+        } else {
+          const float4 e = ec[j][slot];
+          f = e.x * pd[j] - bet[j] * Ap + e.y * tb.x + e.z * tb.y;
+        }
+        if (SRC) f += bbr[j] * tb.x + bbi[j] * tb.y;
+        pd[j] = f;
+      }
+#pragma unroll
+      for (int j = 0; j < NY; ++j) {
+        vre[j] += tb.z * p[j];
+        vim[j] += tb.w * pd[j];
+      }
+      tb = tn;
+    }
+#pragma unroll
+    for (int j = 0; j < NY; ++j) {
+      vre[j] *= scale;  // u^{(m+1)} = (2/N_t) v
+      vim[j] *= scale;
+    }
+    m_done = m + 1;
+    if (a.wh_tol > 0.0) {
+      double dn = 0.0, un = 0.0;
+#pragma unroll
+      for (int j = 0; j < NY; ++j) {
+        const float2 o = uo[j][lane];
+        const double dr = (double)vre[j] - (double)o.x, di = (double)vim[j] - (double)o.y;
+        dn += dr * dr + di * di;
+        un += (double)vre[j] * vre[j] + (double)vim[j] * vim[j];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        dn += __shfl_xor_sync(0xffffffffu, dn, o);
+        un += __shfl_xor_sync(0xffffffffu, un, o);
+      }
+      if (dn <= a.wh_tol * a.wh_tol * un) break;  // warp-uniform after the reduction
+    }
+  }
+
+  // ---- outputs
+  bool bad = false;
+  if (live) {
+#pragma unroll
+    for (int j = 0; j < NY; ++j) {
+      if (!isfinite(vre[j]) || !isfinite(vim[j])) bad = true;
+      if (a.u_sub) {
+        const int64_t n = (int64_t)l * nn + (int64_t)j * nlx + i;
+        a.u_sub[2 * n] = (double)vre[j];
+        a.u_sub[2 * n + 1] = (double)vim[j];
+      }
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.flags, 1);
+  if (lane == 0 && a.wh_iter_max) {
+    atomicMax(a.wh_iter_max, m_done);
+    atomicAdd(a.wh_iter_sum, (unsigned long long)m_done);
+  }
+  const int NE = a.NE;
+  const double* kedgeL = a.kedge + (int64_t)l * 4 * NE;
+  // S / N edges: lane i holds node (i, 0) and (i, NY-1)
+  auto put = [&](int e, int t, bool has, double ur, double ui) {
+    const bool iface = (e == 0) ? ifW : (e == 1) ? ifE : (e == 2) ? ifS : ifN;
+    const int len = (e < 2) ? NY : nlx;
+    if (iface) {
+      const int r = (e == 0) ? l - 1 : (e == 1) ? l + 1 : (e == 2) ? l - a.Sx : l + a.Sx;
+      double* dst = a.lam_out + 2 * (((int64_t)r * 4 + (e ^ 1)) * NE + t);
+      if (t < len && has) {
+        const double kk = kedgeL[e * NE + t];
+        const double lr = lamL[2 * (e * NE + t)], li = lamL[2 * (e * NE + t) + 1];
+        dst[0] = -lr + 2.0 * kk * ui;
+        dst[1] = -li - 2.0 * kk * ur;
+      } else {
+        dst[0] = 0.0;
+        dst[1] = 0.0;
+      }
+    } else {
+      double* dst = a.lam_out + 2 * (((int64_t)l * 4 + e) * NE + t);
+      dst[0] = 0.0;
+      dst[1] = 0.0;
+    }
+  };
+  for (int t = lane; t < NE; t += 32) {
+    // lane t < nlx holds column t: rows 0 and NY-1 are in its registers only
+    // for t == lane, which holds in the first pass (nlx <= 32)
+    const bool mine = t == lane && live;
+    put(2, t, mine, mine ? (double)vre[0] : 0.0, mine ? (double)vim[0] : 0.0);
+    put(3, t, mine, mine ? (double)vre[NY - 1] : 0.0, mine ? (double)vim[NY - 1] : 0.0);
+  }
+  // W / E edges: columns 0 and nlx-1 hold every row
+  if (lane == 0 || lane == nlx - 1) {
+#pragma unroll
+    for (int j = 0; j < NY; ++j) {
+      if (lane == 0) put(0, j, true, (double)vre[j], (double)vim[j]);
+      if (lane == nlx - 1) put(1, j, true, (double)vre[j], (double)vim[j]);
+    }
+  }
+  if (lane == 0) {
+    for (int t = NY; t < NE; ++t) {
+      put(0, t, false, 0.0, 0.0);
+      put(1, t, false, 0.0, 0.0);
+    }
+  }
+}
+
+}  // namespace warp_sweep
+}  // namespace hz

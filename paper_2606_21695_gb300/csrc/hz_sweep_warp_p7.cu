@@ -1,0 +1,26 @@
+// Warp-per-subdomain sweep instantiations for degree 7.
+#include "hz_sweep_warp.cuh"
+
+namespace hz {
+namespace warp_sweep {
+namespace {
+template <int P, int SY>
+hz_status launch(const WarpSweepArgs& a, cudaStream_t st) {
+  const int blocks = (a.L + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (a.base.rhs) sweep_warp_kernel<P, SY, true><<<blocks, kWarpsPerBlock * 32, 0, st>>>(a);
+  else sweep_warp_kernel<P, SY, false><<<blocks, kWarpsPerBlock * 32, 0, st>>>(a);
+  note_launch();
+  HZ_CUDA(cudaGetLastError());
+  return HZ_OK;
+}
+}  // namespace
+
+hz_status launch_p7(int sy, const WarpSweepArgs& a, cudaStream_t st) {
+  switch (sy) {
+    case 1: return launch<7, 1>(a, st);
+    case 2: return launch<7, 2>(a, st);
+    default: return HZ_ERR_UNSUPPORTED;
+  }
+}
+}  // namespace warp_sweep
+}  // namespace hz

@@ -1,0 +1,92 @@
+"""Batched solves and the request server: every result equals the same
+problem solved alone (bitwise: fixed reduction orders, kernel choice cached
+per shape), admission against the HBM budget, error paths."""
+
+import time
+
+import numpy as np
+import pytest
+
+from workloads import configs
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix():
+    base = configs.config1()
+    return [
+        configs.Workload("mixA", (0, 1, 0, 1), 16, 16, 2, 4, 4, 9.0, "const", (0.3, 0.6), 0.05),
+        configs.Workload("mixB", (0, 1, 0, 1), 12, 12, 3, 4, 4, 14.0, "channel", (0.5, 0.3), 0.03),
+        configs.Workload("mixC", (0, 1, 0, 1), 8, 16, 4, 4, 8, 6.0, "random", (0.4, 0.5), 0.05, corr_len=0.3),
+        configs.scaled(base, 16, 16, 8, 8, name="mixD"),
+    ]
+
+
+def _opts(hz):
+    return hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=1e-8)
+
+
+def test_batch_equals_individual_solves(hz):
+    from paper_2606_21695_gb300.api import Case
+
+    cases = [Case(wl) for wl in _mix()]
+    solo = []
+    for c in cases:
+        st, u, rep = hz.hz_solve(c.pr, _opts(hz), n=c.n)
+        assert st == hz.HZ_OK, rep
+        assert rep["sweep_variant"] in (1, 2, 3)
+        solo.append(u.copy())
+    st, sts, us, reps = hz.hz_solve_batch([c.pr for c in cases], [c.n for c in cases], _opts(hz), max_concurrent=4)
+    assert st == hz.HZ_OK and all(s == hz.HZ_OK for s in sts)
+    for k in range(len(cases)):
+        assert reps[k]["rel_residual"] <= 1e-8
+        assert np.array_equal(us[k], solo[k]), k
+
+
+def test_server_results_same_alone_and_in_mix(hz):
+    from paper_2606_21695_gb300.api import Case
+
+    cases = [Case(wl) for wl in _mix()]
+    solo = [hz.hz_solve(c.pr, _opts(hz), n=c.n)[1].copy() for c in cases]
+    srv = hz.hz_server_create(0, 8 << 30)
+    try:
+        tickets = []
+        for rnd in range(2):  # requests arrive while others run
+            for c in cases:
+                tickets.append((hz.hz_server_submit(srv, c.pr, _opts(hz)), c))
+            time.sleep(0.01)
+        for t, c in tickets:
+            done, st, u, rep = hz.hz_server_poll(srv, t, -1, n=c.n)
+            assert done and st == hz.HZ_OK
+            k = cases.index(c)
+            assert np.array_equal(u, solo[k])
+        stats = hz.hz_server_stats(srv)
+        assert stats["p99_ms"] >= stats["p50_ms"] > 0 and stats["solves_per_s"] > 0
+        assert stats["hbm_in_use"] == 0
+        with pytest.raises(hz.HzError) as e:
+            hz.hz_server_poll(srv, 987654, 0, n=cases[0].n)
+        assert e.value.status == hz.HZ_ERR_NOT_FOUND
+    finally:
+        hz.hz_server_destroy(srv)
+
+
+def test_server_admission_refuses_over_budget_without_disturbing_others(hz):
+    from paper_2606_21695_gb300.api import Case
+
+    small = Case(_mix()[0])
+    big = Case(configs.scaled(configs.config2(), 64, 64, 8, 8, name="big"))
+    srv = hz.hz_server_create(0, 64 << 20)  # 64 MiB: the small problem fits, the big one does not
+    try:
+        t = hz.hz_server_submit(srv, small.pr, _opts(hz))
+        with pytest.raises(hz.HzError) as e:
+            hz.hz_server_submit(srv, big.pr, _opts(hz))
+        assert e.value.status == hz.HZ_ERR_BUSY
+        done, st, u, rep = hz.hz_server_poll(srv, t, -1, n=small.n)
+        assert done and st == hz.HZ_OK and rep["rel_residual"] <= 1e-8
+        # a poll with zero timeout on an unfinished request reports not done
+        t2 = hz.hz_server_submit(srv, small.pr, _opts(hz))
+        done0, _, _, _ = hz.hz_server_poll(srv, t2, 0, n=small.n)
+        done1, st1, _, _ = hz.hz_server_poll(srv, t2, -1, n=small.n)
+        assert done1 and st1 == hz.HZ_OK
+    finally:
+        hz.hz_server_destroy(srv)
