@@ -289,6 +289,7 @@ def run_ours(args):
             "time_to_tol_s": {"fp32_refine": elapsed / args.steps, "fp64": fp64["seconds"] if fp64 else None},
             "fp64_solve": fp64,
             "solve": {"sweeps_per_solve": sweeps / args.steps, "rel_residual_max": max(res),
+                      "sweep_kernel": {1: "block", 2: "warp", 3: "cluster"}.get(reports[0]["sweep_variant"]),
                       "refinements": reports[0]["refinements"], "gmres_iters": reports[0]["gmres_iters"],
                       "dof_updates_per_solve": dof / args.steps},
             "roofline": {"kernel": "sweep_kernel<float,3,1> (one launch = one DD sweep)", "bound": "alu",

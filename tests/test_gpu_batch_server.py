@@ -73,9 +73,9 @@ def test_server_results_same_alone_and_in_mix(hz):
 def test_server_admission_refuses_over_budget_without_disturbing_others(hz):
     from paper_2606_21695_gb300.api import Case
 
-    small = Case(_mix()[0])
-    big = Case(configs.scaled(configs.config2(), 64, 64, 8, 8, name="big"))
-    srv = hz.hz_server_create(0, 64 << 20)  # 64 MiB: the small problem fits, the big one does not
+    small = Case(_mix()[0])  # 1089 nodes, 16 subdomains: about 2 MiB of device state
+    big = Case(configs.scaled(configs.config2(), 128, 128, 8, 8, name="big"))  # 148k nodes, 256 subdomains: ~40 MiB
+    srv = hz.hz_server_create(0, 16 << 20)  # 16 MiB: the small problem fits, the big one does not
     try:
         t = hz.hz_server_submit(srv, small.pr, _opts(hz))
         with pytest.raises(hz.HzError) as e:
