@@ -216,6 +216,24 @@ HZ_API hz_status hz_rhs(hz_problem pr, double* b, void* stream);
  * r = -K u).  Uses library-owned scratch for the reduction. */
 HZ_API hz_status hz_residual(hz_problem pr, const double* b, const double* u, double* r, double* norms2, void* stream);
 
+/* Same as hz_residual, for callers that cannot allocate device memory (code
+ * running inside someone else's CUDA graph capture, hosts whose allocator
+ * belongs to another runtime, real-time loops that must not synchronise):
+ * this entry point allocates nothing.  (The paper has no counterpart; it is
+ * an interface convenience.)  The caller owns every array: c (n real wave
+ * speeds), b (n complex, may be NULL = zero), u (n complex), r (n complex,
+ * output), norms2 (2 doubles: ||r||^2, ||b||^2), all device memory on the
+ * current device; mesh is the host-side mesh description.  Block partial
+ * sums live in a fixed array in the library's device memory (2 MiB, held by
+ * every device that loads the library until the process exits), which limits
+ * the mesh to 2^17 blocks of 32 x 8 nodes (about 33.5 M nodes); larger meshes
+ * return HZ_ERR_UNSUPPORTED before anything is launched.  The first call on a
+ * device looks up that array's device address (set-up): make it before any
+ * stream capture.  All calls share the array, so calls that overlap on the
+ * GPU race; serialise them on one stream. */
+HZ_API hz_status hz_residual_noalloc(hz_mesh mesh, double omega, const double* c, const double* b, const double* u,
+                                     double* r, double* norms2, void* stream);
+
 /* u += mass-weighted average of the subdomain copies u_sub (the inverse of the
  * splitting of a global right-hand side by lumped-mass share). */
 HZ_API hz_status hz_assemble_add(hz_problem pr, const double* u_sub, double* u, void* stream);

@@ -89,6 +89,7 @@ def load():
         "hz_rhs": (i32, [vp, vp, vp]),
         "hz_residual": (i32, [vp, vp, vp, vp, vp, vp]),
         "hz_assemble_add": (i32, [vp, vp, vp, vp]),
+        "hz_residual_noalloc": (i32, [vp, d, vp, vp, vp, vp, vp, vp]),
         "hz_server_create": (i32, [i32, u64, C.POINTER(vp)]),
         "hz_server_submit": (i32, [vp, vp, C.POINTER(hz_solve_opts), C.POINTER(u64)]),
         "hz_server_poll": (i32, [vp, u64, i32, dp, C.POINTER(hz_solve_report), C.POINTER(i32)]),
@@ -108,7 +109,7 @@ def exported_names():
     return ["hz_default_opts", "hz_last_error", "hz_kernel_launches", "hz_mesh_create", "hz_mesh_num_nodes", "hz_mesh_node_coords",
             "hz_mesh_destroy", "hz_problem_create", "hz_problem_set", "hz_problem_set_device", "hz_problem_destroy",
             "hz_problem_nt", "hz_solve", "hz_solve_device", "hz_solve_batch", "hz_lambda_size", "hz_prepare", "hz_sweep", "hz_rhs",
-            "hz_residual", "hz_assemble_add", "hz_server_create", "hz_server_submit", "hz_server_poll",
+            "hz_residual", "hz_residual_noalloc", "hz_assemble_add", "hz_server_create", "hz_server_submit", "hz_server_poll",
             "hz_server_stats", "hz_server_destroy"]
 
 
@@ -282,6 +283,12 @@ def hz_rhs(pr, b, stream=None):
 
 def hz_residual(pr, b, u, r, norms2=None, stream=None):
     _check(load().hz_residual(pr, _ptr(b), _ptr(u), _ptr(r), _ptr(norms2), _stream(stream)))
+
+
+def hz_residual_noalloc(mesh, omega, c, b, u, r, norms2, stream=None):
+    """Residual without device allocation; every array is the caller's."""
+    _check(load().hz_residual_noalloc(mesh, omega, _ptr(c), _ptr(b), _ptr(u), _ptr(r), _ptr(norms2),
+                                      _stream(stream)))
 
 
 def hz_assemble_add(pr, u_sub, u, stream=None):
