@@ -46,9 +46,15 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 time-to-tolerance leg")
+    ap.add_argument("--no-trials", action="store_true", help="skip the FP16/BF16 sweep-error trials")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
-    ap.add_argument("--mode", choices=["solve", "sweep"], default="solve",
-                    help="sweep: only run --sweeps DD sweeps of the workload (for ncu captures)")
+    ap.add_argument("--mode", choices=["solve", "sweep", "batch", "serve"], default="solve",
+                    help="sweep: only run --sweeps DD sweeps of the workload (for ncu captures); "
+                         "batch: batched solves of the multi-problem workload; serve: served request stream")
+    ap.add_argument("--batch", type=int, default=12, help="problems in --mode batch")
+    ap.add_argument("--requests", type=int, default=40, help="arrivals in --mode serve")
+    ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals per second in --mode serve")
+    ap.add_argument("--baseline-requests", type=int, default=12)
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--wh-iters", type=int, default=20)
@@ -272,6 +278,25 @@ def run_ours(args):
             fp64 = {"seconds": e0.elapsed_time(e1) * 1e-3, "status": hz.STATUS_NAMES[st64],
                     "sweeps": rep64["sweeps"], "rel_residual": rep64["rel_residual"],
                     "dof_updates_per_s": rep64["dof_updates"] / (e0.elapsed_time(e1) * 1e-3)}
+        # 16-bit trials: one sweep each, error against the FP64 sweep (which is
+        # checked against the oracle by the test suite)
+        trials = None
+        if not args.no_trials:
+            nt_ = reports[0]["nt"]
+            nl = hz.hz_lambda_size(case.pr)
+            gen = torch.Generator(device="cuda").manual_seed(1)
+            lin = torch.randn(2 * nl, dtype=torch.float64, device="cuda", generator=gen) * 1e-2
+            outs = {}
+            for name, prec in (("fp64", hz.HZ_FP64), ("fp32", hz.HZ_FP32_REFINE), ("fp16", hz.HZ_FP16_TRIAL),
+                               ("bf16", hz.HZ_BF16_TRIAL)):
+                lo = torch.zeros_like(lin)
+                hz.hz_sweep(case.pr, prec, nt_, opts.wh_iters, 0.0, lin, lo)
+                outs[name] = lo
+            torch.cuda.synchronize()
+            ref = outs["fp64"]
+            den = float(ref.abs().max())
+            trials = {k: {"sweep_rel_err_vs_fp64": float((outs[k] - ref).abs().max()) / den}
+                      for k in ("fp32", "fp16", "bf16")}
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             v, desc, el = oracle_sample(wl, args.cpu_sample_s)
@@ -298,6 +323,7 @@ def run_ours(args):
                          "algorithmic": f"{flops_per_update} flop/DOF-update x {dof_per_launch:.4g} DOF-updates/launch",
                          "avg_launch_ms": avg_launch * 1e3, "launch_share": sweep_s / elapsed},
             "cpu_baseline": cpu,
+            "precision_trials": trials,
             "e2e": {"value": e2e_dof / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
             "gpu_launches": int(launches),
@@ -363,10 +389,132 @@ def run_sweeps(args):
     return {"mode": "sweep", "sweeps": args.sweeps, "nt": nt, "precision": args.precision, "wh_iters": args.wh_iters}
 
 
+def _cheap_cfg4(k):
+    """The k least expensive problems of the batched workload sampler (cost =
+    global nodes x estimated N_t); the full sampler reaches N_t ~ 10^4 on
+    512^2 degree-5 meshes, far beyond a bench run."""
+    from workloads import configs
+
+    lam = {1: 8.0, 2: 48.0, 3: 148.6, 4: 366.7, 5: 783.9}  # lambda_max h^2 of the 2D GLL operator
+    rows = []
+    for w in configs.config4():
+        cmax = 1.5 if w.speed_kind == "random" else 1.0
+        dt = 0.9 * 2 / (cmax * math.sqrt(lam[w.P]) * w.nx)
+        nt = math.ceil(2 * math.pi / w.omega / dt)
+        rows.append(((w.nx * w.P + 1) ** 2 * nt, w))
+    rows.sort(key=lambda r: r[0])
+    return [w for _, w in rows[:k]]
+
+
+def run_batch(args):
+    """--mode batch: the cheapest problems of the batched workload solved one
+    at a time and together (hz_solve_batch); FP32 sweeps + FP64 refinement."""
+    import torch
+
+    import paper_2606_21695_gb300 as hz
+    from paper_2606_21695_gb300.api import Case
+
+    wls = _cheap_cfg4(args.batch)
+    cases = [Case(w) for w in wls]
+    opts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, max_sweeps=5000)
+    hz.hz_solve_batch([c.pr for c in cases], [c.n for c in cases], opts, 8, want_u=False)  # warm-up / autotune
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq = [hz.hz_solve(c.pr, opts, n=c.n) for c in cases]
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    st, sts, _, reps = hz.hz_solve_batch([c.pr for c in cases], [c.n for c in cases], opts, 8, want_u=False)
+    t_bat = time.perf_counter() - t0
+    dof = sum(r["dof_updates"] for r in reps)
+    return {"mode": "batch", "problems": [w.name for w in wls], "solves": len(cases),
+            "sequential_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat,
+            "solves_per_s_batched": len(cases) / t_bat, "dof_updates_per_s_batched": dof / t_bat,
+            "max_rel_residual": max(r["rel_residual"] for r in reps),
+            "statuses": [hz.STATUS_NAMES[s] for s in sts],
+            "sequential_residual_max": max(s[2]["rel_residual"] for s in seq)}
+
+
+def run_serve(args):
+    """--mode serve: Poisson arrivals (seeded, mean args.rate per second) of
+    solve requests drawn from the cheapest problems of the batched workload;
+    with probability 0.2 a request is a group of 8 sources on one mesh and
+    frequency.  Reports p50/p99 latency and solves/s, and the same stream
+    solved one at a time in plain FP64 for comparison."""
+    import numpy as np
+    import torch
+
+    import paper_2606_21695_gb300 as hz
+    from paper_2606_21695_gb300.api import Case
+    from workloads import fields
+
+    pool = _cheap_cfg4(8)
+    cases = {w.name: Case(w) for w in pool}
+    rng = np.random.default_rng(5)
+    reqs = []
+    t = 0.0
+    for _ in range(args.requests):
+        t += rng.exponential(1.0 / args.rate)
+        w = pool[int(rng.integers(len(pool)))]
+        k = 8 if rng.uniform() < 0.2 else 1
+        for _ in range(k):
+            reqs.append((t, w, tuple(rng.uniform(0.2, 0.8, 2))))
+    opts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, max_sweeps=5000)
+    # per-request problems (sources differ), built before the clock starts
+    probs = []
+    for _, w, ctr in reqs:
+        c = cases[w.name]
+        X, Y = np.meshgrid(c.gx, c.gy)
+        f = fields.gaussian_source(X, Y, ctr, w.src_width).astype(complex)
+        pr = hz.hz_problem_create(c.mesh, 0)
+        hz.hz_problem_set(pr, hz.HZ_WAVE_SPEED, c.c.ravel())
+        hz.hz_problem_set(pr, hz.HZ_OMEGA, np.array([w.omega]))
+        hz.hz_problem_set(pr, hz.HZ_SOURCE, f.ravel())
+        probs.append((pr, c.n))
+    for w in pool:  # autotune the shapes outside the timed stream
+        c = cases[w.name]
+        hz.hz_solve(c.pr, opts, n=c.n)
+    os.environ.setdefault("HZ_SERVER_WORKERS", "8")
+    srv = hz.hz_server_create(0, 150 << 30)  # HBM admission budget of the served workload
+    t0 = time.perf_counter()
+    tickets = []
+    for (ta, _, _), (pr, n) in zip(reqs, probs):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        tickets.append((hz.hz_server_submit(srv, pr, opts), n))
+    res = []
+    for tk, n in tickets:
+        done, st, _, rep = hz.hz_server_poll(srv, tk, -1, n=None)
+        res.append(rep["rel_residual"])
+    wall = time.perf_counter() - t0
+    stats = hz.hz_server_stats(srv)
+    hz.hz_server_destroy(srv)
+    # baseline: the same stream one request at a time, plain FP64
+    o64 = hz.hz_default_opts(precision=hz.HZ_FP64, tol=TOL, max_sweeps=5000)
+    nb = min(len(probs), args.baseline_requests)
+    t0 = time.perf_counter()
+    for pr, n in probs[:nb]:
+        hz.hz_solve(pr, o64, n=n)
+    t_base = (time.perf_counter() - t0) / nb
+    for pr, _ in probs:
+        hz.hz_problem_destroy(pr)
+    return {"mode": "serve", "requests": len(reqs), "arrival_rate_per_s": args.rate, "wall_s": wall,
+            "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "solves_per_s": len(reqs) / wall,
+            "max_rel_residual": max(res), "pool": [w.name for w in pool],
+            "one_at_a_time_fp64_s_per_solve": t_base, "one_at_a_time_fp64_solves_per_s": 1.0 / t_base,
+            "one_at_a_time_fp64_sample": nb}
+
+
 def main():
     args = parse()
     if args.mode == "sweep":
         print(json.dumps(run_sweeps(args)), flush=True)
+        return
+    if args.mode == "batch":
+        print(json.dumps(run_batch(args)), flush=True)
+        return
+    if args.mode == "serve":
+        print(json.dumps(run_serve(args)), flush=True)
         return
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:

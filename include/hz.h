@@ -69,8 +69,10 @@ typedef enum {
 } hz_status;
 
 /* Precision of the subdomain WaveHoltz loop (Sec. 7).  The outer GMRES,
- * refinement and global residual are always FP64. */
-typedef enum { HZ_FP64 = 0, HZ_FP32_REFINE = 1 } hz_precision;
+ * refinement and global residual are always FP64.  The two trials keep the
+ * wave state p, p-dot rounded to 16 bits after every update (arithmetic and
+ * filter sums in FP32); they exist to report their error, not for speed. */
+typedef enum { HZ_FP64 = 0, HZ_FP32_REFINE = 1, HZ_FP16_TRIAL = 2, HZ_BF16_TRIAL = 3 } hz_precision;
 
 /* Outer iteration on the transmission data (Sec. 3).
  * GMRES: complex GMRES(m) on (I - S) lambda = g (S: homogeneous sweep).
@@ -101,6 +103,9 @@ typedef struct {
   double inner_tol;      /* relative tolerance of each DD solve (GMRES on lambda) */
   int32_t max_refine;    /* maximum FP64 refinement steps */
   int32_t autotune;      /* 1: time the sweep kernel variants once per subdomain shape, use the fastest */
+  int32_t wh_adaptive;   /* 1: per refinement step, WaveHoltz stops at tolerance clamp(0.1 * current
+                            relative residual, wh_tol (or 1e-6), 1e-2), at most wh_iters iterations
+                            (the variable inner tolerance of Sec. 5 / Sec. 8) */
 } hz_solve_opts;
 
 typedef struct {

@@ -19,7 +19,7 @@ _LIB_PATH = os.path.join(_HERE, "_lib", "libhz.so")
 
 HZ_OK, HZ_ERR_INVALID_ARG, HZ_ERR_OOM, HZ_ERR_CUDA, HZ_ERR_NOT_CONVERGED = 0, 1, 2, 3, 4
 HZ_ERR_DIVERGED, HZ_ERR_TIMEOUT, HZ_ERR_BUSY, HZ_ERR_NOT_FOUND, HZ_ERR_INTERNAL, HZ_ERR_UNSUPPORTED = 5, 6, 7, 8, 9, 10
-HZ_FP64, HZ_FP32_REFINE = 0, 1
+HZ_FP64, HZ_FP32_REFINE, HZ_FP16_TRIAL, HZ_BF16_TRIAL = 0, 1, 2, 3
 HZ_OUTER_GMRES, HZ_OUTER_PLAIN, HZ_OUTER_RGMRES = 0, 1, 2
 HZ_WAVE_SPEED, HZ_OMEGA, HZ_SOURCE, HZ_BOUNDARY = 0, 1, 2, 3
 
@@ -38,7 +38,7 @@ class hz_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("max_sweeps", C.c_int32), ("outer", C.c_int32),
                 ("gmres_restart", C.c_int32), ("wh_iters", C.c_int32), ("wh_tol", C.c_double),
                 ("nt_override", C.c_int32), ("cfl", C.c_double), ("inner_tol", C.c_double),
-                ("max_refine", C.c_int32), ("autotune", C.c_int32)]
+                ("max_refine", C.c_int32), ("autotune", C.c_int32), ("wh_adaptive", C.c_int32)]
 
 
 class hz_solve_report(C.Structure):

@@ -69,6 +69,7 @@ double max_eig_1d(const Geom& g, int n_el, double h);  // largest eig of W^-1 K,
 struct SweepArgs {
   int nlx, nly, NE, Sx, Sy, sxe, sye, NXg, NS, snxP, snyP;
   int ty_force;  // block kernel rows per thread: 0 = by size, 1 = P, 2 = 2P
+  int round_mode;  // FP32 block kernel: 0 none, 1 round p and p-dot to FP16, 2 to BF16 (trials)
   int Nt, m_wh;
   double wh_tol, sigma, omega, cpi, spi, two_over_nt;
   double kxs, kys, hx2, hy2;  // 2/hx, 2/hy, hx/2, hy/2
@@ -98,11 +99,12 @@ struct WarpSweepArgs {
   SweepArgs base;
   int L;
   float wyr[kWarpMaxRows];                     // hy/2 * (w_a [own element] + w_P [element below])
-  float kyr[kWarpMaxRows][2 * kMaxP + 1];      // assembled 1D y-stiffness row, taps -P..P (reference scale)
+  float kyr[kWarpMaxRows][2 * kMaxP + 1];      // assembled 1D y-stiffness row (taps -P..P) x (2/hy) / Wy_row
 };
-// Returns HZ_ERR_UNSUPPORTED (without launching) when no warp variant for
-// (P, sub_ny) was compiled or the subdomain has more than 32 node columns.
-hz_status launch_sweep_warp(int P, int sy, const WarpSweepArgs& a, cudaStream_t st);
+// Register-resident sweep with h warps per subdomain (1, 2 or 4).  Returns
+// HZ_ERR_UNSUPPORTED (without launching) when no variant for (P, sub_ny, h)
+// was compiled or the subdomain has more than 32 node columns.
+hz_status launch_sweep_warp(int P, int sy, int h, const WarpSweepArgs& a, cudaStream_t st);
 
 // FP32 sweep of one subdomain per thread-block cluster (column bands, halo
 // exchange through distributed shared memory).  HZ_ERR_UNSUPPORTED when no

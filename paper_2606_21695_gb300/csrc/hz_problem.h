@@ -53,7 +53,8 @@ constexpr int kVariantAuto = 0, kVariantBlock = 1, kVariantWarp = 2, kVariantClu
 int sweep_variant();
 struct Choice {
   int variant;  // kVariantBlock / kVariantWarp / kVariantCluster
-  int ty;       // block kernel rows per thread (0 = by size, 1 = P, 2 = 2P)
+  int ty;       // block kernel: rows per thread (0 = by size, 1 = P, 2 = 2P);
+                // register-resident kernel: warps per subdomain (0/1, 2, 4)
 };
 std::string tune_key(const Geom& g, int precision);
 bool lookup_choice(const std::string& key, Choice* out);

@@ -200,7 +200,9 @@ void warp_rows(const Geom& g, WarpSweepArgs* w) {
       double v = 0.0;
       if (own && ay + t >= 0 && ay + t <= P) v += g.Kref[ay * (P + 1) + ay + t];
       if (below && t <= 0) v += g.Kref[P * (P + 1) + P + t];
-      w->kyr[j][t + P] = (float)v;
+      // divided by the row's lumped weight: the kernels use beta' = beta Wx Wy
+      const double wy = g.hy / 2.0 * ((own ? g.w[ay] : 0.0) + (below ? g.w[P] : 0.0));
+      w->kyr[j][t + P] = wy > 0.0 ? (float)(v * (2.0 / g.hy) / wy) : 0.f;
     }
   }
 }
@@ -240,7 +242,7 @@ hz_status launch_choice(Problem& pr, const SweepArgs& a0, Choice c, bool fp32, c
     w.base = a0;
     w.L = g.L;
     warp_rows(g, &w);
-    s = launch_sweep_warp(g.P, g.sny, w, st);
+    s = launch_sweep_warp(g.P, g.sny, c.ty > 0 ? c.ty : 1, w, st);
   } else if (c.variant == kVariantCluster) {
     if (!fp32) return HZ_ERR_UNSUPPORTED;
     s = launch_sweep_cluster(g.P, a0, g.L, st);
@@ -323,7 +325,9 @@ hz_status autotune(Problem& pr, int precision, int nt, int m_wh, cudaStream_t st
   const bool fp32 = precision == HZ_FP32_REFINE;
   const SweepArgs a = make_sweep_args(pr, fp32, nt, m_wh, 0.0, pr.xv.as<double>(), pr.tv.as<double>(), nullptr, nullptr);
   std::vector<Choice> cands;
-  if (fp32) cands = {{kVariantWarp, 0}, {kVariantBlock, 1}, {kVariantBlock, 2}, {kVariantCluster, 0}};
+  if (fp32)
+    cands = {{kVariantWarp, 1}, {kVariantWarp, 2}, {kVariantWarp, 4}, {kVariantBlock, 1}, {kVariantBlock, 2},
+             {kVariantCluster, 0}};
   else cands = {{kVariantBlock, 1}, {kVariantBlock, 2}};
   cudaEvent_t e0, e1;
   HZ_CUDA(cudaEventCreate(&e0));
@@ -362,9 +366,11 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
   HZ_TRY(ensure_flags(pr));
   const Geom& g = pr.g;
   if (m_wh < 0) return fail(HZ_ERR_INVALID_ARG, "wh_iters must be >= 0");
-  const bool fp32 = precision == HZ_FP32_REFINE;
-  if (precision != HZ_FP64 && precision != HZ_FP32_REFINE) return fail(HZ_ERR_INVALID_ARG, "unknown precision");
-  const SweepArgs a = make_sweep_args(pr, fp32, nt, m_wh, wh_tol, lam_in, lam_out, rhs, u_sub);
+  if (precision < HZ_FP64 || precision > HZ_BF16_TRIAL) return fail(HZ_ERR_INVALID_ARG, "unknown precision");
+  const bool trial = precision == HZ_FP16_TRIAL || precision == HZ_BF16_TRIAL;
+  const bool fp32 = precision != HZ_FP64;
+  SweepArgs a = make_sweep_args(pr, fp32, nt, m_wh, wh_tol, lam_in, lam_out, rhs, u_sub);
+  if (trial) a.round_mode = precision == HZ_FP16_TRIAL ? 1 : 2;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (pr.time_sweeps) {
     if (pr.ev_used + 2 > pr.events.size()) {
@@ -384,17 +390,21 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
   // FP32 -> warp-per-subdomain kernel when compiled for the shape, else one
   // block per subdomain when it fits in 256 threads, else a cluster of
   // blocks, else the block kernel with up to 1024 threads; FP64 -> block.
-  const int want = sweep_variant();
+  const int want = trial ? kVariantBlock : sweep_variant();  // 16-bit trials run on the block kernel
   Choice ch{};
   bool have = false;
   if (want == kVariantAuto && pr.autotune && lookup_choice(tune_key(pr.g, precision), &ch)) have = true;
+  (void)trial;
   hz_status ls = HZ_ERR_UNSUPPORTED;
   if (have) {
     ls = launch_choice(pr, a, ch, fp32, st);
     if (ls != HZ_OK && ls != HZ_ERR_UNSUPPORTED) return ls;
   }
   if (ls == HZ_ERR_UNSUPPORTED && fp32 && (want == kVariantAuto || want == kVariantWarp)) {
-    ls = launch_choice(pr, a, Choice{kVariantWarp, 0}, fp32, st);
+    // HZ_SWEEP_WARPS=2|4 forces warps per subdomain of the register-resident kernel (tests)
+    const char* hw = std::getenv("HZ_SWEEP_WARPS");
+    const int h = hw ? std::atoi(hw) : 1;
+    ls = launch_choice(pr, a, Choice{kVariantWarp, h}, fp32, st);
     if (ls != HZ_OK && ls != HZ_ERR_UNSUPPORTED) return ls;
     if (ls != HZ_OK && want == kVariantWarp) return fail(HZ_ERR_UNSUPPORTED, "no warp sweep variant for this subdomain");
   }
@@ -570,19 +580,28 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
           // w = v_j - S v_j
           HZ_CUDA(cudaMemcpyAsync(w, vj, vb, cudaMemcpyDeviceToDevice, c.st));
           HZ_TRY(launch_axpby(-1.0, tv, 1.0, w, n2, c.st));
-          // classical Gram-Schmidt, two passes
+          // classical Gram-Schmidt; the batched dot product also returns ||w||^2
+          // (V_{j+1} = w is the next vector in the basis array), and a second
+          // pass runs only when the first lost more than half of ||w|| in
+          // norm (Daniel-Gragg-Kaufman-Stewart criterion)
           const int nv = j + 1;
-          HZ_TRY(dots(c, V, n2, nv, w, real, 0));
+          HZ_TRY(dots(c, V, n2, nv + 1, w, real, 0));
           HZ_TRY(launch_multi_axpy(V, n2, nv, pr.small.as<double>(), w, n2, real, c.st));
-          HZ_TRY(dots(c, V, n2, nv, w, real, 2 * (m + 1)));
-          HZ_TRY(launch_multi_axpy(V, n2, nv, pr.small.as<double>() + 2 * (m + 1), w, n2, real, c.st));
           HZ_TRY(dots(c, w, 0, 1, w, real, 4 * (m + 1)));
           HZ_TRY(fetch(c, 4 * (m + 1) + 2, hbuf, flags));
           c.rep.gmres_iters++;
-          for (int i = 0; i <= j; ++i)
-            H[(size_t)i * m + j] = cplx(hbuf[2 * i] + hbuf[2 * (m + 1) + 2 * i],
-                                        hbuf[2 * i + 1] + hbuf[2 * (m + 1) + 2 * i + 1]);
-          const double hnext = std::sqrt(std::max(0.0, hbuf[4 * (m + 1)]));
+          for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = cplx(hbuf[2 * i], hbuf[2 * i + 1]);
+          double wn2_before = hbuf[2 * nv];
+          double hn2 = hbuf[4 * (m + 1)];
+          if (hn2 < 0.5 * wn2_before) {
+            HZ_TRY(dots(c, V, n2, nv, w, real, 2 * (m + 1)));
+            HZ_TRY(launch_multi_axpy(V, n2, nv, pr.small.as<double>() + 2 * (m + 1), w, n2, real, c.st));
+            HZ_TRY(dots(c, w, 0, 1, w, real, 4 * (m + 1)));
+            HZ_TRY(fetch(c, 4 * (m + 1) + 2, hbuf, flags));
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += cplx(hbuf[2 * (m + 1) + 2 * i], hbuf[2 * (m + 1) + 2 * i + 1]);
+            hn2 = hbuf[4 * (m + 1)];
+          }
+          const double hnext = std::sqrt(std::max(0.0, hn2));
           // ||(I - S) v|| for a unit v is O(1) for a stable subdomain solve; growth by
           // many orders of magnitude means the leapfrog is unstable (time step too large)
           if (!(hnext < kGrowthLimit) || !(std::abs(H[(size_t)j * m + j]) < kGrowthLimit))
@@ -660,7 +679,7 @@ hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report*
   HZ_TRY(pr.hsmall.ensure(8192 * sizeof(double)));
   HZ_TRY(prepare(pr, nt, st));
   HZ_TRY(ensure_flags(pr));
-  pr.autotune = o.autotune != 0 && sweep_variant() == kVariantAuto;
+  pr.autotune = o.autotune != 0 && sweep_variant() == kVariantAuto && o.precision <= HZ_FP32_REFINE;
   if (pr.autotune) HZ_TRY(autotune(pr, o.precision, nt, o.wh_iters, st));
   HZ_CUDA(cudaMemsetAsync(pr.flags.ptr, 0, 64, st));
   HZ_TRY(rhs(pr, pr.bvec.as<double>(), st));
@@ -692,7 +711,12 @@ hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report*
       result = fail(HZ_ERR_NOT_CONVERGED, "tolerance not reached within the refinement / sweep budget");
       break;
     }
-    hz_status s = dd_solve(c, pr.rvec.as<double>(), u);
+    // variable inner tolerance (Sec. 5 end, Sec. 8): loose subdomain solves while
+    // the global residual is large, tightened as it falls
+    hz_solve_opts oi = o;
+    if (o.wh_adaptive) oi.wh_tol = std::min(1e-2, std::max(o.wh_tol > 0.0 ? o.wh_tol : 1e-6, 0.1 * rel));
+    Ctx ci{pr, oi, nt, st, rep, c.n2};
+    hz_status s = dd_solve(ci, pr.rvec.as<double>(), u);
     if (s != HZ_OK && s != HZ_ERR_NOT_CONVERGED) return s;
     rep.refinements++;
   }

@@ -31,6 +31,8 @@
 // Epilogue: lambda_{r,l} = -lambda_{l,r} - 2 i (omega/c) u_l on each
 // interface (eq. (lambda-iteration), sign read as -2ik), written into the
 // neighbour's slot; slots of outer edges are zeroed.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -56,6 +58,15 @@ template <>
 struct Tab4T<double> {
   using type = Dbl4;
 };
+
+// 16-bit storage trials: the wave state is rounded to FP16 / BF16 after every
+// update (the filter sums stay in the working precision).
+template <typename Real>
+__device__ __forceinline__ Real round16(Real v, int mode) {
+  if (mode == 1) return Real(__half2float(__float2half_rn((float)v)));
+  if (mode == 2) return Real(__bfloat162float(__float2bfloat16_rn((float)v)));
+  return v;
+}
 
 template <typename Real>
 __device__ __forceinline__ Real kref(const SweepArgs& a, int k);
@@ -183,6 +194,10 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(const __grid_constant__ Swe
       Real* bufc = cur ? buf1 : buf0;
 #pragma unroll
       for (int r = 0; r < RY; ++r) p[r] += sigma * pd[r];
+      if (a.round_mode) {
+#pragma unroll
+        for (int r = 0; r < RY; ++r) p[r] = round16(p[r], a.round_mode);
+      }
       if (active) {
 #pragma unroll
         for (int r = 0; r < RY; ++r) bufc[(j0 + r + P) * colsP + i + P] = p[r];
@@ -226,7 +241,7 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(const __grid_constant__ Swe
           sx += kx[tt] * row[tt];
         }
         const Real Ap = wy[r] * sx + wxy * sy[r];
-        pd[r] = alp[r] * pd[r] - bet[r] * Ap + bbr[r] * tb.x + bbi[r] * tb.y;
+        pd[r] = round16(alp[r] * pd[r] - bet[r] * Ap + bbr[r] * tb.x + bbi[r] * tb.y, a.round_mode);
         vre[r] += tb.z * p[r];
         vim[r] += tb.w * pd[r];
       }

@@ -20,7 +20,9 @@
 namespace hz {
 namespace warp_sweep {
 
-constexpr int kWarpsPerBlock = 4;
+// One subdomain per block: 1024 subdomains spread as 6-7 blocks per SM over
+// 152 SMs, instead of whole 4-subdomain blocks landing unevenly.
+constexpr int kWarpsPerBlock = 1;
 
 // Is tap t of assembled 1D row j structurally non-zero?  Row j lies in
 // element j/P at position j%P; class-0 rows also touch the element below.
@@ -51,6 +53,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) sweep_warp_kernel(const _
   const int ax = i % P, ex = i / P;
   const bool own_x = live && ex < a.sxe;
   const bool left_x = live && (ax == 0) && (ex >= 1);
+  // with beta' = beta Wx Wy the stiffness terms are divided by the lumped
+  // weights: (A p)/(Wx Wy) = (Kx p)/Wx + (Ky p)/Wy, so no weight multiplies remain
+  const double wx_lane = a.hx2 * ((own_x ? a.w[ax] : 0.0) + (left_x ? a.w[P] : 0.0));
   float kx[NK];
 #pragma unroll
   for (int tt = 0; tt < NK; ++tt) {
@@ -59,9 +64,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) sweep_warp_kernel(const _
     const int b = ax + off;
     if (own_x && b >= 0 && b <= P) v += a.Kref[ax * (P + 1) + b];
     if (left_x && off <= 0) v += a.Kref[P * (P + 1) + (off + P)];
-    kx[tt] = (float)(v * a.kxs);
+    kx[tt] = live ? (float)(v * a.kxs / wx_lane) : 0.f;
   }
-  const float wxy = (float)(a.kys * a.hx2 * ((own_x ? a.w[ax] : 0.0) + (left_x ? a.w[P] : 0.0)));
 
   // ---- node coefficients and right-hand side.  alpha != 1 and (without a
   // source) b != 0 only on the subdomain edges: rows 0 and NY-1 keep them in
@@ -100,7 +104,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) sweep_warp_kernel(const _
       if (j == 0 && ifS) { br += a.wxs[i] * lamL[2 * (2 * a.NE + i)]; bi += a.wxs[i] * lamL[2 * (2 * a.NE + i) + 1]; }
       if (j == NY - 1 && ifN) { br += a.wxs[i] * lamL[2 * (3 * a.NE + i)]; bi += a.wxs[i] * lamL[2 * (3 * a.NE + i) + 1]; }
     }
-    bet[j] = (float)be;
+    bet[j] = (float)(be * wx_lane * x.wyr[j]);  // beta' = beta Wx Wy
     const float fbr = (float)(be * br), fbi = (float)(be * bi);
     if (SRC) {
       bbr[j] = fbr;
@@ -147,21 +151,20 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) sweep_warp_kernel(const _
       for (int j = 0; j < NY; ++j) p[j] += sigma * pd[j];
 #pragma unroll
       for (int j = 0; j < NY; ++j) {
-        // x: neighbours in the same row from neighbouring lanes
-        float sx = kx[P] * p[j];
+        // (A p)_j / (Wx Wy): y taps from registers (compile-time sparsity,
+        // coefficients in the constant bank), then x taps from neighbour lanes
+        float Ap = kx[P] * p[j];
+#pragma unroll
+        for (int t = -P; t <= P; ++t) {
+          if (tap(P, SY, j, t) && j + t >= 0 && j + t < NY) Ap += x.kyr[j][t + P] * p[j + t];
+        }
 #pragma unroll
         for (int t = 1; t <= P; ++t) {
           const float up = __shfl_down_sync(0xffffffffu, p[j], t);  // lane i+t
           const float dn = __shfl_up_sync(0xffffffffu, p[j], t);    // lane i-t
-          sx += kx[P + t] * up + kx[P - t] * dn;
+          Ap += kx[P + t] * up;
+          Ap += kx[P - t] * dn;
         }
-        // y: assembled row j, compile-time sparsity
-        float sy = 0.f;
-#pragma unroll
-        for (int t = -P; t <= P; ++t) {
-          if (tap(P, SY, j, t) && j + t >= 0 && j + t < NY) sy += x.kyr[j][t + P] * p[j + t];
-        }
-        const float Ap = x.wyr[j] * sx + wxy * sy;
         float f;
         if (j == 0) {
           f = al0 * pd[j] - bet[j] * Ap + b0r * tb.x + b0i * tb.y;

@@ -1,26 +1,35 @@
-// Warp-per-subdomain sweep instantiations for degree 2.
+// Register-resident sweep instantiations for degree 2: one warp per
+// subdomain (h = 1) and, for the larger shapes, h = 2 or 4 warps per
+// subdomain (row bands).
+#include "hz_sweep_band.cuh"
 #include "hz_sweep_warp.cuh"
 
 namespace hz {
 namespace warp_sweep {
 namespace {
-template <int P, int SY>
+template <int P, int SY, int H>
 hz_status launch(const WarpSweepArgs& a, cudaStream_t st) {
-  const int blocks = (a.L + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  if (a.base.rhs) sweep_warp_kernel<P, SY, true><<<blocks, kWarpsPerBlock * 32, 0, st>>>(a);
-  else sweep_warp_kernel<P, SY, false><<<blocks, kWarpsPerBlock * 32, 0, st>>>(a);
+  if constexpr (H == 1) {
+    const int blocks = (a.L + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (a.base.rhs) sweep_warp_kernel<P, SY, true><<<blocks, kWarpsPerBlock * 32, 0, st>>>(a);
+    else sweep_warp_kernel<P, SY, false><<<blocks, kWarpsPerBlock * 32, 0, st>>>(a);
+  } else {
+    const int blocks = a.L;  // one subdomain (H warps) per block
+    if (a.base.rhs) band_sweep::sweep_band_kernel<P, SY, true, H><<<blocks, H * 32, 0, st>>>(a);
+    else band_sweep::sweep_band_kernel<P, SY, false, H><<<blocks, H * 32, 0, st>>>(a);
+  }
   note_launch();
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
 }  // namespace
 
-hz_status launch_p2(int sy, const WarpSweepArgs& a, cudaStream_t st) {
+hz_status launch_p2(int sy, int h, const WarpSweepArgs& a, cudaStream_t st) {
   switch (sy) {
-    case 1: return launch<2, 1>(a, st);
-    case 2: return launch<2, 2>(a, st);
-    case 4: return launch<2, 4>(a, st);
-    case 8: return launch<2, 8>(a, st);
+    case 1: if (h == 1) return launch<2, 1, 1>(a, st); return HZ_ERR_UNSUPPORTED;
+    case 2: if (h == 1) return launch<2, 2, 1>(a, st); return HZ_ERR_UNSUPPORTED;
+    case 4: if (h == 1) return launch<2, 4, 1>(a, st); return HZ_ERR_UNSUPPORTED;
+    case 8: if (h == 1) return launch<2, 8, 1>(a, st); if (h == 2) return launch<2, 8, 2>(a, st); if (h == 4) return launch<2, 8, 4>(a, st); return HZ_ERR_UNSUPPORTED;
     default: return HZ_ERR_UNSUPPORTED;
   }
 }

@@ -101,6 +101,8 @@ def _run_sweep(hz, case, pr, precision, nt, m_wh, lam, with_rhs, wh_tol=0.0):
 
 
 LAYOUTS = [
+    (16, 16, 8, 8, 3),  # the benchmark's subdomain shape (25 x 25 nodes), 2x2 subdomains
+    (32, 16, 8, 8, 2),  # 17 x 17 nodes: four-band variant for P = 2
     (8, 8, 4, 4, 2),   # 2x2 subdomains (cross point)
     (6, 6, 2, 2, 3),   # 3x3 subdomains, P = 3
     (8, 4, 2, 4, 1),   # 4x1 strips, P = 1
@@ -130,11 +132,16 @@ def test_sweep_fp64_matches_oracle(hz, nx, ny, sx, sy, P):
     case.close()
 
 
-@pytest.fixture(params=["auto", "block"])
+@pytest.fixture(params=["auto", "block", "warp2", "warp4"])
 def sweep_variant(request, monkeypatch):
-    """auto: the warp-per-subdomain FP32 kernel where compiled, else the block
-    kernel; block: the block kernel everywhere."""
-    monkeypatch.setenv("HZ_SWEEP_VARIANT", request.param)
+    """auto: the register-resident kernel (one warp per subdomain) where
+    compiled, else the block kernel; block: the block kernel everywhere;
+    warp2 / warp4: two / four warps per subdomain where compiled (others fall
+    back to the default choice)."""
+    if request.param.startswith("warp"):
+        monkeypatch.setenv("HZ_SWEEP_WARPS", request.param[4:])
+    else:
+        monkeypatch.setenv("HZ_SWEEP_VARIANT", request.param)
     return request.param
 
 
@@ -415,3 +422,41 @@ def test_config1_full_solve_matches_direct(hz):
     err = np.linalg.norm(u - ud) / np.linalg.norm(ud)
     print("cfg1 fp64", rep, "err", err)
     assert st == hz.HZ_OK and rep["rel_residual"] <= 1e-10 and err < 1e-8
+
+
+@pytest.mark.parametrize("trial", ["fp16", "bf16"])
+def test_16bit_trials_report_their_error(hz, trial):
+    """FP16 / BF16 storage of the wave state: reported with its error against
+    the FP64 oracle (no accuracy target; sanity bounds only)."""
+    wl = _wl(8, 8, 4, 4, 3)
+    case, pr = _pair(hz, wl, g_seed=1)
+    nt = hz.hz_problem_nt(case.pr)
+    lam = _rand_lam(pr, 12)
+    prec = hz.HZ_FP16_TRIAL if trial == "fp16" else hz.HZ_BF16_TRIAL
+    got_l, got_u = _run_sweep(hz, case, pr, prec, nt, 5, lam, True)
+    f32_l, f32_u = _run_sweep(hz, case, pr, hz.HZ_FP32_REFINE, nt, 5, lam, True)
+    ref_l, ref_u, _ = pr.sweep(lam, pr.rhs(), nt, 5, want_u=True)
+    e16, e32 = _rel(got_u, ref_u), _rel(f32_u, ref_u)
+    print(f"{trial} trial sweep rel err {e16:.2e} (fp32 {e32:.2e})")
+    assert np.isfinite(e16) and e32 < e16 < 0.5
+    st, u, rep = hz.hz_solve(case.pr, hz.hz_default_opts(precision=prec, tol=1e-8, max_sweeps=600, max_refine=8),
+                             n=case.n)
+    ud = pr.direct_solve().ravel()
+    print(f"{trial} trial solve: status {st} residual {rep['rel_residual']:.2e} "
+          f"err vs direct {np.linalg.norm(u - ud) / np.linalg.norm(ud):.2e} sweeps {rep['sweeps']}")
+    assert np.all(np.isfinite(u))
+
+
+def test_adaptive_waveholtz_tolerance_solve(hz):
+    """Variable inner tolerance: WaveHoltz stops per subdomain at a tolerance
+    that follows the global residual; the solve still reaches 1e-8 and agrees
+    with the direct solution."""
+    wl = configs.scaled(configs.config1(), 16, 16, 4, 4, name="cfg1_16x16")
+    case, pr = _pair(hz, wl)
+    opts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=1e-8, wh_iters=40, wh_adaptive=1, inner_tol=1e-2)
+    st, u, rep = hz.hz_solve(case.pr, opts, n=case.n)
+    ud = pr.direct_solve().ravel()
+    err = np.linalg.norm(u - ud) / np.linalg.norm(ud)
+    print("adaptive", rep, err)
+    assert st == hz.HZ_OK and rep["rel_residual"] <= 1e-8 and err < 1e-6
+    assert rep["wh_iters_max"] <= 40
