@@ -122,7 +122,7 @@ typedef struct {
 } hz_solve_report;
 
 /* Defaults: FP64, tol 1e-8, 2000 sweeps, GMRES(60), 20 WaveHoltz iterations,
- * no wh_tol, CFL 0.9, inner_tol 1e-3, 20 refinements, autotune on. */
+ * no wh_tol, CFL 0.9, inner_tol 1e-2, 20 refinements, autotune on. */
 HZ_API void hz_default_opts(hz_solve_opts* opts);
 
 /* Copies the calling thread's last error message (NUL-terminated, truncated

@@ -232,25 +232,37 @@ __global__ void assemble_add_kernel(const __grid_constant__ AssembleArgs a, cons
 }
 
 // ---- Krylov vector kernels (vectors of n2 doubles = n2/2 complex values)
-__global__ void multi_dot_kernel(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ w,
-                                 int64_t n2, int real_dot, double* __restrict__ part) {
-  const int k = blockIdx.y;
-  const double* v = V + (int64_t)k * ld;
-  double s[2] = {0.0, 0.0};
-  const int64_t nc = n2 / 2;
-  const double2* v2 = reinterpret_cast<const double2*>(v);
+// One block per contiguous chunk of the vectors: the chunk of w is staged in
+// shared memory once, then the block's warps take the basis vectors in turn
+// (coalesced reads of each V_k chunk, warp reduction), so every element of V
+// and w is read from memory once per call.  part[(blk * nv + k) * 2 + {0, 1}].
+constexpr int kDotWarps = 8;
+__global__ void __launch_bounds__(kDotWarps * 32)
+    multi_dot_kernel(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ w, int64_t nc,
+                     int chunk, int real_dot, double* __restrict__ part) {
+  extern __shared__ double2 ws[];
+  const int64_t r0 = (int64_t)blockIdx.x * chunk;
+  const int rows = (int)((nc - r0) < chunk ? (nc - r0) : chunk);
   const double2* w2 = reinterpret_cast<const double2*>(w);
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += (int64_t)gridDim.x * blockDim.x) {
-    const double2 a = v2[q], b = w2[q];
-    s[0] += a.x * b.x + a.y * b.y;  // Re conj(a) b  (= real dot of the pair)
-    if (!real_dot) s[1] += a.x * b.y - a.y * b.x;  // Im conj(a) b
-  }
-  __shared__ double out[2];
-  block_sum<2>(s, out);
-  if (threadIdx.x == 0) {
-    double* p = part + ((int64_t)blockIdx.x * nv + k) * 2;
-    p[0] = out[0];
-    p[1] = out[1];
+  for (int q = threadIdx.x; q < rows; q += blockDim.x) ws[q] = w2[r0 + q];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = warp; k < nv; k += kDotWarps) {
+    const double2* vk = reinterpret_cast<const double2*>(V + (int64_t)k * ld) + r0;
+    double sr = 0.0, si = 0.0;
+#pragma unroll 4
+    for (int q = lane; q < rows; q += 32) {
+      const double2 a = vk[q], b = ws[q];
+      sr += a.x * b.x + a.y * b.y;  // Re conj(a) b
+      si += a.x * b.y - a.y * b.x;  // Im conj(a) b
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if (lane == 0) {
+      double* p = part + ((int64_t)blockIdx.x * nv + k) * 2;
+      p[0] = sr;
+      p[1] = real_dot ? 0.0 : si;
+    }
   }
 }
 
@@ -263,6 +275,7 @@ __global__ void multi_axpy_kernel(const double* __restrict__ V, int64_t ld, int 
   double2* w2 = reinterpret_cast<double2*>(w);
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += (int64_t)gridDim.x * blockDim.x) {
     double2 acc = w2[q];
+#pragma unroll 4
     for (int k = 0; k < nv; ++k) {
       const double2 v = reinterpret_cast<const double2*>(V + (int64_t)k * ld)[q];
       const double hr = hs[2 * k], hi = real_coef ? 0.0 : hs[2 * k + 1];
@@ -276,6 +289,16 @@ __global__ void multi_axpy_kernel(const double* __restrict__ V, int64_t ld, int 
 __global__ void axpby_kernel(double a, const double* __restrict__ x, double b, double* __restrict__ y, int64_t n2) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n2; q += (int64_t)gridDim.x * blockDim.x)
     y[q] = a * x[q] + b * y[q];
+}
+
+// y = x / sqrt(n2[0]) (0 if the norm is 0): normalises the next Krylov vector
+// on the device, without a round trip to the host.
+__global__ void scale_inv_norm_kernel(const double* __restrict__ x, const double* __restrict__ n2,
+                                      double* __restrict__ y, int64_t n) {
+  const double v = n2[0];
+  const double s = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    y[q] = s * x[q];
 }
 
 int grid_for(int64_t n, int threads) {
@@ -347,12 +370,23 @@ hz_status launch_assemble_add(const AssembleArgs& a, const double* u_sub, double
   return HZ_OK;
 }
 
-int vec_blocks(int64_t n2) { return grid_for(n2 / 2, kRedThreads) > 304 ? 304 : grid_for(n2 / 2, kRedThreads); }
+// blocks for multi_dot: ~2 per SM, chunks of at most 4096 complex entries (64 KB of shared memory)
+int vec_blocks(int64_t n2) {
+  const int64_t nc = n2 / 2;
+  int64_t nb = 304;
+  if ((nc + nb - 1) / nb > 4096) nb = (nc + 4095) / 4096;
+  if (nb > nc) nb = nc > 0 ? nc : 1;
+  return (int)nb;
+}
 
 hz_status launch_multi_dot(const double* V, int64_t ld, int nv, const double* w, int64_t n2, bool real_dot,
                            double* part, int nblocks, cudaStream_t st) {
-  dim3 grd(nblocks, nv);
-  multi_dot_kernel<<<grd, kRedThreads, 0, st>>>(V, ld, nv, w, n2, real_dot ? 1 : 0, part);
+  const int64_t nc = n2 / 2;
+  const int chunk = (int)((nc + nblocks - 1) / nblocks);
+  const size_t smem = (size_t)chunk * sizeof(double2);
+  if (smem > 48 * 1024)
+    HZ_CUDA(cudaFuncSetAttribute(multi_dot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  multi_dot_kernel<<<nblocks, kDotWarps * 32, smem, st>>>(V, ld, nv, w, nc, chunk, real_dot ? 1 : 0, part);
   note_launch();
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
@@ -362,6 +396,13 @@ hz_status launch_multi_axpy(const double* V, int64_t ld, int nv, const double* h
                             bool real_coef, cudaStream_t st) {
   const int g = grid_for(n2 / 2, 256);
   multi_axpy_kernel<<<g, 256, (size_t)2 * nv * sizeof(double), st>>>(V, ld, nv, h, w, n2, real_coef ? 1 : 0);
+  note_launch();
+  HZ_CUDA(cudaGetLastError());
+  return HZ_OK;
+}
+
+hz_status launch_scale_inv_norm(const double* x, const double* norm2, double* y, int64_t n2, cudaStream_t st) {
+  scale_inv_norm_kernel<<<grid_for(n2, 256), 256, 0, st>>>(x, norm2, y, n2);
   note_launch();
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;

@@ -168,8 +168,8 @@ hz_status launch_multi_axpy(const double* V, int64_t ld, int nv, const double* h
                             bool real_coef, cudaStream_t st);
 // y = alpha * x (alpha real, on device at *alpha_inv as 1/alpha); y may alias x
 hz_status launch_scale(const double* x, const double* norm, double* y, int64_t n2, cudaStream_t st);
-// y = x (copy)
-hz_status launch_copy(const double* x, double* y, int64_t n2, cudaStream_t st);
+// y = x / sqrt(*norm2) with norm2 in device memory (0 if the norm is 0)
+hz_status launch_scale_inv_norm(const double* x, const double* norm2, double* y, int64_t n2, cudaStream_t st);
 // y = x - y  (for r = g - (I - S) lam: helper)   y = a*x + b*y
 hz_status launch_axpby(double a, const double* x, double b, double* y, int64_t n2, cudaStream_t st);
 

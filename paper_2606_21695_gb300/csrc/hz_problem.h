@@ -17,6 +17,8 @@ struct HostBuf {
   HostBuf& operator=(const HostBuf&) = delete;
   ~HostBuf();
   hz_status ensure(size_t nbytes);
+  template <typename T>
+  T* as() const { return static_cast<T*>(ptr); }
 };
 
 }  // namespace hz
@@ -39,8 +41,9 @@ struct hz_problem_s {
   // leapfrog coefficients for prepared_nt
   hz::DevBuf beta64, alpha64, beta32, alpha32, kedge, tab64, tab32;
   // solver workspace
-  hz::DevBuf bvec, rvec, uvec, usub, gv, xv, tv, V, part, small, flags;
-  hz::HostBuf hsmall;
+  hz::DevBuf bvec, rvec, uvec, usub, gv, xv, tv, V, part, small, flags, hcol;
+  hz::HostBuf hsmall, hcol_host;
+  std::vector<cudaEvent_t> gm_events;  // one per Arnoldi step of a cycle
   // per-sweep CUDA events while a solve runs (report.sweep_seconds)
   bool time_sweeps = false;
   size_t ev_used = 0;

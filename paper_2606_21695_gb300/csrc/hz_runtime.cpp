@@ -484,12 +484,16 @@ hz_status fetch(Ctx& c, int nd, double* host, int* flags_host) {
 }
 
 // out[0..2nv) = reduced dots of V_0..V_{nv-1} with w (device small buffer at offset off).
-hz_status dots(Ctx& c, const double* V, int64_t ld, int nv, const double* w, bool real, int off) {
+hz_status dots_to(Ctx& c, const double* V, int64_t ld, int nv, const double* w, bool real, double* out) {
   Problem& pr = c.pr;
   const int nb = vec_blocks(c.n2);
   HZ_TRY(pr.part.ensure((size_t)nb * nv * 2 * sizeof(double) + 64));
   HZ_TRY(launch_multi_dot(V, ld, nv, w, c.n2, real, pr.part.as<double>(), nb, c.st));
-  return launch_reduce_partials(pr.part.as<double>(), nb, 2 * nv, pr.small.as<double>() + off, c.st);
+  return launch_reduce_partials(pr.part.as<double>(), nb, 2 * nv, out, c.st);
+}
+
+hz_status dots(Ctx& c, const double* V, int64_t ld, int nv, const double* w, bool real, int off) {
+  return dots_to(c, V, ld, nv, w, real, c.pr.small.as<double>() + off);
 }
 
 // Outer-iteration sweeps keep one sweep of the budget in reserve for the
@@ -571,36 +575,64 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
         std::fill(gvec.begin(), gvec.end(), cplx(0.0));
         gvec[0] = beta;
         int k = 0;
-        for (int j = 0; j < m; ++j) {
+        // Pipelined Arnoldi: step j's device work (sweep, two classical
+        // Gram-Schmidt passes, norm, normalisation of V_{j+1} by a device-side
+        // 1/||w||) needs nothing from the host, so step j+1 is enqueued before
+        // the host waits for column j of the Hessenberg matrix; the host's
+        // Givens update overlaps the next sweep.  A converged cycle leaves one
+        // enqueued step unused.
+        const size_t CS = (size_t)4 * m + 8;  // per column: pass-1 dots (m+2), pass-2 dots (m+1), norm: complex
+        HZ_TRY(pr.hcol.ensure((size_t)(m + 1) * CS * sizeof(double)));
+        HZ_TRY(pr.hcol_host.ensure((size_t)(m + 1) * (CS + 4) * sizeof(double)));
+        while (pr.gm_events.size() < (size_t)(m + 1)) {
+          cudaEvent_t e;
+          HZ_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+          pr.gm_events.push_back(e);
+        }
+        double* hd = pr.hcol.as<double>();
+        double* hh = pr.hcol_host.as<double>();
+        auto enqueue = [&](int j) -> hz_status {
           double* vj = V + (size_t)j * n2;
           double* w = V + (size_t)(j + 1) * n2;
           hz_status s = do_sweep(c, vj, tv, nullptr, nullptr);
-          if (s == HZ_ERR_NOT_CONVERGED) { done = true; break; }
-          HZ_TRY(s);
-          // w = v_j - S v_j
+          if (s != HZ_OK) return s;
           HZ_CUDA(cudaMemcpyAsync(w, vj, vb, cudaMemcpyDeviceToDevice, c.st));
-          HZ_TRY(launch_axpby(-1.0, tv, 1.0, w, n2, c.st));
-          // classical Gram-Schmidt; the batched dot product also returns ||w||^2
-          // (V_{j+1} = w is the next vector in the basis array), and a second
-          // pass runs only when the first lost more than half of ||w|| in
-          // norm (Daniel-Gragg-Kaufman-Stewart criterion)
+          HZ_TRY(launch_axpby(-1.0, tv, 1.0, w, n2, c.st));  // w = v_j - S v_j
           const int nv = j + 1;
-          HZ_TRY(dots(c, V, n2, nv + 1, w, real, 0));
-          HZ_TRY(launch_multi_axpy(V, n2, nv, pr.small.as<double>(), w, n2, real, c.st));
-          HZ_TRY(dots(c, w, 0, 1, w, real, 4 * (m + 1)));
-          HZ_TRY(fetch(c, 4 * (m + 1) + 2, hbuf, flags));
-          c.rep.gmres_iters++;
-          for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = cplx(hbuf[2 * i], hbuf[2 * i + 1]);
-          double wn2_before = hbuf[2 * nv];
-          double hn2 = hbuf[4 * (m + 1)];
-          if (hn2 < 0.5 * wn2_before) {
-            HZ_TRY(dots(c, V, n2, nv, w, real, 2 * (m + 1)));
-            HZ_TRY(launch_multi_axpy(V, n2, nv, pr.small.as<double>() + 2 * (m + 1), w, n2, real, c.st));
-            HZ_TRY(dots(c, w, 0, 1, w, real, 4 * (m + 1)));
-            HZ_TRY(fetch(c, 4 * (m + 1) + 2, hbuf, flags));
-            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += cplx(hbuf[2 * (m + 1) + 2 * i], hbuf[2 * (m + 1) + 2 * i + 1]);
-            hn2 = hbuf[4 * (m + 1)];
+          double* col = hd + (size_t)j * CS;
+          HZ_TRY(dots_to(c, V, n2, nv, w, real, col));
+          HZ_TRY(launch_multi_axpy(V, n2, nv, col, w, n2, real, c.st));
+          HZ_TRY(dots_to(c, V, n2, nv, w, real, col + 2 * (m + 2)));
+          HZ_TRY(launch_multi_axpy(V, n2, nv, col + 2 * (m + 2), w, n2, real, c.st));
+          double* nrm = col + 2 * (m + 2) + 2 * (m + 1);
+          HZ_TRY(dots_to(c, w, 0, 1, w, real, nrm));
+          HZ_TRY(launch_scale_inv_norm(w, nrm, w, n2, c.st));
+          double* hslot = hh + (size_t)j * (CS + 4);
+          HZ_CUDA(cudaMemcpyAsync(hslot, col, CS * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+          HZ_CUDA(cudaMemcpyAsync(hslot + CS, pr.flags.ptr, 16, cudaMemcpyDeviceToHost, c.st));
+          HZ_CUDA(cudaEventRecord(pr.gm_events[j], c.st));
+          return HZ_OK;
+        };
+        hz_status es = enqueue(0);
+        if (es == HZ_ERR_NOT_CONVERGED) break;
+        HZ_TRY(es);
+        for (int j = 0; j < m; ++j) {
+          bool next = false;
+          if (j + 1 < m) {
+            es = enqueue(j + 1);
+            if (es == HZ_OK) next = true;
+            else if (es != HZ_ERR_NOT_CONVERGED) return es;
           }
+          HZ_CUDA(cudaEventSynchronize(pr.gm_events[j]));
+          const double* hslot = hh + (size_t)j * (CS + 4);
+          int fl[4];
+          std::memcpy(fl, hslot + CS, 16);
+          if (fl[0] & 1) return fail(HZ_ERR_DIVERGED, "non-finite values in the subdomain solve (time step too large?)");
+          c.rep.gmres_iters++;
+          for (int i = 0; i <= j; ++i)
+            H[(size_t)i * m + j] = cplx(hslot[2 * i] + hslot[2 * (m + 2) + 2 * i],
+                                        hslot[2 * i + 1] + hslot[2 * (m + 2) + 2 * i + 1]);
+          const double hn2 = hslot[2 * (m + 2) + 2 * (m + 1)];
           const double hnext = std::sqrt(std::max(0.0, hn2));
           // ||(I - S) v|| for a unit v is O(1) for a stable subdomain solve; growth by
           // many orders of magnitude means the leapfrog is unstable (time step too large)
@@ -613,13 +645,13 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
             H[(size_t)(i + 1) * m + j] = -std::conj(sn[i]) * a + cs[i] * b;
           }
           const cplx a = H[(size_t)j * m + j];
-          const double r = std::sqrt(std::norm(a) + hnext * hnext);
+          const double rr = std::sqrt(std::norm(a) + hnext * hnext);
           if (std::abs(a) == 0.0) {
             cs[j] = 0.0;
             sn[j] = 1.0;
           } else {
-            cs[j] = std::abs(a) / r;
-            sn[j] = (a / std::abs(a)) * hnext / r;
+            cs[j] = std::abs(a) / rr;
+            sn[j] = (a / std::abs(a)) * hnext / rr;
           }
           H[(size_t)j * m + j] = cs[j] * a + sn[j] * hnext;
           gvec[j + 1] = -std::conj(sn[j]) * gvec[j];
@@ -627,8 +659,10 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
           k = j + 1;
           const double res = std::abs(gvec[j + 1]);
           if (res <= tol * gnorm || hnext == 0.0) { done = true; break; }
-          if (c.rep.sweeps + 1 >= c.o.max_sweeps) { done = true; break; }
-          HZ_TRY(launch_axpby(0.0, w, 1.0 / hnext, w, n2, c.st));
+          if (!next) {
+            if (j + 1 < m) done = true;  // sweep budget exhausted
+            break;
+          }
         }
         if (k > 0) {
           // back substitution R y = gvec, then x += V y  (multi_axpy subtracts, so pass -y)
@@ -848,7 +882,7 @@ void hz_default_opts(hz_solve_opts* o) {
   o->wh_tol = 0.0;
   o->nt_override = 0;
   o->cfl = 0.9;
-  o->inner_tol = 1e-3;
+  o->inner_tol = 1e-2;
   o->max_refine = 20;
   o->autotune = 1;
 }
@@ -972,6 +1006,7 @@ void hz_problem_destroy(hz_problem pr) {
   if (!pr) return;
   cudaSetDevice(pr->device);
   for (cudaEvent_t e : pr->events) cudaEventDestroy(e);
+  for (cudaEvent_t e : pr->gm_events) cudaEventDestroy(e);
   if (pr->stream) cudaStreamDestroy(pr->stream);
   delete pr;
 }

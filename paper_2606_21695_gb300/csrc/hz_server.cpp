@@ -135,6 +135,8 @@ struct hz_server_s {
       const uint64_t freed = job->bytes;
       for (cudaEvent_t e : pr.events) cudaEventDestroy(e);
       pr.events.clear();
+      for (cudaEvent_t e : pr.gm_events) cudaEventDestroy(e);
+      pr.gm_events.clear();
       if (pr.stream) cudaStreamDestroy(pr.stream);
       pr.stream = nullptr;
       job->pr.reset();
