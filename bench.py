@@ -58,8 +58,9 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--wh-iters", type=int, default=20)
-    ap.add_argument("--workload", choices=["cfg1", "cfg2", "cfg3"], default="cfg2",
-                    help="solve mode: cfg2 is the benchmark workload; cfg1/cfg3 are reported separately")
+    ap.add_argument("--workload", choices=["cfg1", "cfg2", "cfg3", "cfg3s"], default="cfg2",
+                    help="cfg2 is the benchmark workload; cfg1/cfg3 are reported separately; cfg3s is the "
+                         "cfg3 physics and subdomain shape on a 256x256 mesh (for profiling)")
     return ap.parse_args()
 
 
@@ -163,6 +164,14 @@ def oracle_sample(wl, seconds, nsub_max=1024):
     return dof / el, desc, el
 
 
+def workload(name):
+    from workloads import configs
+
+    if name == "cfg3s":
+        return configs.scaled(configs.config3(), 256, 256, 32, 32, name="cfg3_scaled_256x256_p4_sub32")
+    return {"cfg1": configs.config1, "cfg2": configs.config2, "cfg3": configs.config3}[name]()
+
+
 def combine_ranks(elapsed, work, device):
     """Whole-job figures over all ranks: the slowest rank's time and the sum
     of the work (weak scaling: every rank solves its own problem)."""
@@ -193,7 +202,7 @@ def run_ours(args):
     from paper_2606_21695_gb300.api import Case, boundary_vector
     from workloads import configs
 
-    wl = {"cfg1": configs.config1, "cfg2": configs.config2, "cfg3": configs.config3}[args.workload]()
+    wl = workload(args.workload)
     case = Case(wl, device=local)
     n = case.n
     stream = torch.cuda.current_stream()
@@ -382,7 +391,7 @@ def run_sweeps(args):
     from paper_2606_21695_gb300.api import Case
     from workloads import configs
 
-    wl = configs.config2()
+    wl = workload(args.workload)
     case = Case(wl)
     nt = hz.hz_problem_nt(case.pr)
     nl = hz.hz_lambda_size(case.pr)
@@ -390,11 +399,25 @@ def run_sweeps(args):
     lin = torch.randn(2 * nl, dtype=torch.float64, device="cuda", generator=g) * 1e-2
     lout = torch.zeros_like(lin)
     prec = hz.HZ_FP32_REFINE if args.precision == "fp32" else hz.HZ_FP64
-    for _ in range(args.sweeps):
-        hz.hz_sweep(case.pr, prec, nt, args.wh_iters, 0.0, lin, lout)
+    # first sweep untimed (autotuning, if any, and warm-up); the rest timed
+    # on the launching (default) stream
+    hz.hz_sweep(case.pr, prec, nt, args.wh_iters, 0.0, lin, lout)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.sweeps - 1):
+        hz.hz_sweep(case.pr, prec, nt, args.wh_iters, 0.0, lin, lout)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(1, args.sweeps - 1)
+    L = wl.nx // wl.sub_nx * (wl.ny // wl.sub_ny)
+    dof = L * (wl.sub_nx * wl.P + 1) * (wl.sub_ny * wl.P + 1) * (nt - 1) * args.wh_iters
+    flop = 2 * (2 * wl.P + 13) * dof
     case.close()
-    return {"mode": "sweep", "sweeps": args.sweeps, "nt": nt, "precision": args.precision, "wh_iters": args.wh_iters}
+    return {"mode": "sweep", "workload": wl.name, "sweeps": args.sweeps, "nt": nt, "precision": args.precision,
+            "wh_iters": args.wh_iters, "ms_per_sweep": ms if args.sweeps > 1 else None,
+            "dof_updates_per_sweep": dof, "dof_updates_per_s": dof / (ms * 1e-3) if args.sweeps > 1 else None,
+            "tflops": flop / (ms * 1e-3) / 1e12 if args.sweeps > 1 else None}
 
 
 def _cheap_cfg4(k):
@@ -424,21 +447,33 @@ def run_batch(args):
 
     wls = _cheap_cfg4(args.batch)
     cases = [Case(w) for w in wls]
-    opts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, max_sweeps=5000)
-    hz.hz_solve_batch([c.pr for c in cases], [c.n for c in cases], opts, 8, want_u=False)  # warm-up / autotune
+    opts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, max_sweeps=5000, pack=0)
+    popts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, max_sweeps=5000, pack=1)
+    prs, ns = [c.pr for c in cases], [c.n for c in cases]
+    hz.hz_solve_batch(prs, ns, opts, 8, want_u=False)  # warm-up / autotune
+    hz.hz_solve_batch(prs, ns, popts, 0, want_u=False)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     seq = [hz.hz_solve(c.pr, opts, n=c.n) for c in cases]
     t_seq = time.perf_counter() - t0
     t0 = time.perf_counter()
-    st, sts, _, reps = hz.hz_solve_batch([c.pr for c in cases], [c.n for c in cases], opts, 8, want_u=False)
+    st, sts, _, reps = hz.hz_solve_batch(prs, ns, opts, 8, want_u=False)
     t_bat = time.perf_counter() - t0
+    k0 = hz.hz_kernel_launches()
+    t0 = time.perf_counter()
+    pst, psts, _, preps = hz.hz_solve_batch(prs, ns, popts, 0, want_u=False)
+    t_pack = time.perf_counter() - t0
+    k_pack = hz.hz_kernel_launches() - k0
     dof = sum(r["dof_updates"] for r in reps)
+    pdof = sum(r["dof_updates"] for r in preps)
     return {"mode": "batch", "problems": [w.name for w in wls], "solves": len(cases),
             "sequential_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat,
             "solves_per_s_batched": len(cases) / t_bat, "dof_updates_per_s_batched": dof / t_bat,
-            "max_rel_residual": max(r["rel_residual"] for r in reps),
-            "statuses": [hz.STATUS_NAMES[s] for s in sts],
+            "packed_s": t_pack, "packed_speedup": t_seq / t_pack, "solves_per_s_packed": len(cases) / t_pack,
+            "dof_updates_per_s_packed": pdof / t_pack, "packed_members": sum(r["sweep_variant"] == 4 for r in preps),
+            "packed_kernel_launches": k_pack,
+            "max_rel_residual": max(r["rel_residual"] for r in reps + preps),
+            "statuses": [hz.STATUS_NAMES[s] for s in sts], "packed_statuses": [hz.STATUS_NAMES[s] for s in psts],
             "sequential_residual_max": max(s[2]["rel_residual"] for s in seq)}
 
 

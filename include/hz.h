@@ -106,6 +106,11 @@ typedef struct {
   int32_t wh_adaptive;   /* 1: per refinement step, WaveHoltz stops at tolerance clamp(0.1 * current
                             relative residual, wh_tol (or 1e-6), 1e-2), at most wh_iters iterations
                             (the variable inner tolerance of Sec. 5 / Sec. 8) */
+  int32_t pack;          /* 1: in hz_solve_batch and the server, the sweeps of concurrent solves are
+                            issued together, one packed launch per outer step covering every
+                            subdomain of every member (FP32 sweeps with a fixed WaveHoltz count
+                            on subdomains of at most 32 node columns and degree 1..5; other
+                            solves run unpacked).  Ignored by hz_solve. */
 } hz_solve_opts;
 
 typedef struct {
@@ -117,12 +122,13 @@ typedef struct {
   double seconds;        /* wall time of the solve */
   int64_t dof_updates;   /* sum over sweeps of subdomain nodes x (N_t - 1) x WaveHoltz iterations */
   int32_t gmres_iters;   /* total GMRES iterations */
-  int32_t sweep_variant; /* kernel of the last sweep: 1 block, 2 warp per subdomain, 3 cluster */
+  int32_t sweep_variant; /* kernel of the last sweep: 1 block, 2 warp per subdomain, 3 cluster,
+                            4 packed with other solves */
   double sweep_seconds;  /* device time of the sweep kernels (CUDA events on the solve's stream) */
 } hz_solve_report;
 
 /* Defaults: FP64, tol 1e-8, 2000 sweeps, GMRES(60), 20 WaveHoltz iterations,
- * no wh_tol, CFL 0.9, inner_tol 1e-2, 20 refinements, autotune on. */
+ * no wh_tol, CFL 0.9, inner_tol 1e-2, 20 refinements, autotune on, pack on. */
 HZ_API void hz_default_opts(hz_solve_opts* opts);
 
 /* Copies the calling thread's last error message (NUL-terminated, truncated
@@ -178,9 +184,10 @@ HZ_API hz_status hz_solve_device(hz_problem pr, const hz_solve_opts* opts, doubl
 
 /* Solves count independent problems concurrently on their devices (batched
  * execution, continuous across sizes, degrees and frequencies): at most
- * max_concurrent solves (<= 0: 8) run at once, started in decreasing order of
- * estimated cost; with opts->autotune the sweep kernel of each distinct
- * subdomain shape is timed once first.  u_out[k] (host, n_k complex) may be
+ * max_concurrent solves (<= 0: all of them, up to 64) run at once, started in
+ * decreasing order of estimated cost; with opts->autotune the sweep kernel of
+ * each distinct subdomain shape is timed once first; with opts->pack the
+ * sweeps of the running solves go out as one packed launch per outer step.  u_out[k] (host, n_k complex) may be
  * NULL; reports may be NULL; statuses[k] receives each solve's status.
  * Returns HZ_OK, HZ_ERR_NOT_CONVERGED if any solve ran out of budget, or the
  * first hard error (hz_last_error names the problem). */
@@ -211,6 +218,21 @@ HZ_API hz_status hz_prepare(hz_problem pr, int32_t nt, void* stream);
  * nlx = sub_nx*P+1, subdomain-major).  precision: hz_precision of the loop. */
 HZ_API hz_status hz_sweep(hz_problem pr, int32_t precision, int32_t nt, int32_t wh_iters, double wh_tol,
                    const double* lam_in, double* lam_out, const double* rhs, double* u_sub, void* stream);
+
+/* The same sweep for count problems in one packed launch (the batched form
+ * used by hz_solve_batch and the server; Algorithm 1, Sec. 6): every
+ * subdomain of every problem is swept by one warp, FP32, with nts[k] time
+ * steps per period for problem k and a fixed wh_iters WaveHoltz iterations.
+ * lam_in[k], lam_out[k], rhs[k] (or NULL), u_sub[k] (or NULL): device
+ * buffers of problem k as in hz_sweep.  All problems must live on the
+ * current device.  Returns after the launch has completed on `stream`.
+ * HZ_ERR_UNSUPPORTED (nothing launched) if a problem's subdomain has more
+ * than 32 node columns or a (degree, sub_ny) outside the packed variants
+ * (degree 1 with sub_ny 4, 8, 16; degree 2 with 4, 8; degree 3 with 4, 8;
+ * degrees 4, 5 with 4). */
+HZ_API hz_status hz_sweep_packed(const hz_problem* problems, int32_t count, const int32_t* nts, int32_t wh_iters,
+                                 const double* const* lam_in, double* const* lam_out, const double* const* rhs,
+                                 double* const* u_sub, void* stream);
 
 /* Global weak-form right-hand side b = (f, phi) + <g, phi> (Sec. 4), n complex. */
 HZ_API hz_status hz_rhs(hz_problem pr, double* b, void* stream);

@@ -1,10 +1,12 @@
 // Batched solves: many independent problems on one device at once.
 //
 // Each problem keeps its own device state and stream; a pool of host
-// threads advances the solves concurrently, so the sweep launches of
-// different problems (of different sizes, degrees and frequencies) overlap
-// on the GPU and small problems fill the SMs that one of them alone would
-// leave idle.  Problems start in decreasing order of estimated cost
+// threads advances the solves concurrently.  With opts.pack the sweeps of the
+// running solves go out together: one packed launch per outer step covers
+// every subdomain of every member (different sizes, degrees and frequencies;
+// hz_pack.cpp), otherwise each solve launches its own sweeps and they overlap
+// on the GPU.  Either way small problems fill the SMs that one of them alone
+// would leave idle.  Problems start in decreasing order of estimated cost
 // (longest processing time first: subdomain nodes x (N_t - 1) x WaveHoltz
 // iterations), and the sweep kernel of every distinct subdomain shape is
 // autotuned once, before the concurrent phase, so the timings are not
@@ -14,11 +16,14 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <map>
+#include <memory>
 #include <string>
 #include <thread>
 #include <vector>
 
 #include "hz_internal.h"
+#include "hz_pack.h"
 #include "hz_problem.h"
 
 using namespace hz;
@@ -59,8 +64,18 @@ extern "C" hz_status hz_solve_batch(const hz_problem* problems, int32_t count, c
       HZ_TRY(autotune(pr, o.precision, nts[k], o.wh_iters, pr.stream));
     }
   }
-  int nw = max_concurrent > 0 ? max_concurrent : 8;
+  int nw = max_concurrent > 0 ? max_concurrent : 64;
   nw = std::max(1, std::min(nw, count));
+  // one packer per device in use
+  std::map<int, std::unique_ptr<Packer>> packers;
+  if (o.pack) {
+    for (int k = 0; k < count; ++k) {
+      Problem& pr = *problems[k];
+      if (!Packer::packable(pr, o) || packers.count(pr.device)) continue;
+      HZ_CUDA(cudaSetDevice(pr.device));
+      packers[pr.device] = std::make_unique<Packer>(pr.device);
+    }
+  }
   std::atomic<int> next{0};
   std::vector<std::string> errors(count);
   auto worker = [&]() {
@@ -74,7 +89,17 @@ extern "C" hz_status hz_solve_batch(const hz_problem* problems, int32_t count, c
       const size_t nb = (size_t)pr.g.n * 2 * sizeof(double);
       if (s == HZ_OK) s = pr.uvec.ensure(nb);
       hz_solve_report rep{};
+      Packer* pk = nullptr;
+      if (o.pack && Packer::packable(pr, o)) {
+        pk = packers.at(pr.device).get();
+        pr.packer = pk;
+        pk->join();
+      }
       if (s == HZ_OK) s = solve(pr, o, pr.uvec.as<double>(), &rep, pr.stream);
+      if (pk) {
+        pk->leave();
+        pr.packer = nullptr;
+      }
       if ((s == HZ_OK || s == HZ_ERR_NOT_CONVERGED) && u_out && u_out[k]) {
         if (cudaMemcpyAsync(u_out[k], pr.uvec.ptr, nb, cudaMemcpyDeviceToHost, pr.stream) != cudaSuccess ||
             cudaStreamSynchronize(pr.stream) != cudaSuccess) {

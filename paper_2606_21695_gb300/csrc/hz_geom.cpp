@@ -5,68 +5,11 @@
 #include <string>
 #include <vector>
 
+#include "hz_gll_const.h"
 #include "hz_internal.h"
 
 namespace hz {
 namespace {
-
-// Legendre L_P(x), L_{P-1}(x) by the three-term recurrence.
-void legendre(int P, double x, double* LP, double* LPm1) {
-  double l0 = 1.0, l1 = x;
-  if (P == 0) { *LP = 1.0; *LPm1 = 0.0; return; }
-  for (int k = 1; k < P; ++k) {
-    const double l2 = ((2.0 * k + 1.0) * x * l1 - k * l0) / (k + 1.0);
-    l0 = l1;
-    l1 = l2;
-  }
-  *LP = l1;
-  *LPm1 = l0;
-}
-
-// GLL nodes: endpoints +-1 and the roots of L_P', found by Newton's method on
-// L_P' with L_P'' from the Legendre equation, starting at the Chebyshev-Lobatto
-// points.  Weights w_k = 2 / (P (P+1) L_P(x_k)^2).
-void gll(int P, std::vector<double>& x, std::vector<double>& w) {
-  x.assign(P + 1, 0.0);
-  w.assign(P + 1, 0.0);
-  x[0] = -1.0;
-  x[P] = 1.0;
-  for (int k = 1; k < P; ++k) {
-    double z = -std::cos(M_PI * k / P);
-    for (int it = 0; it < 100; ++it) {
-      double LP, LPm1;
-      legendre(P, z, &LP, &LPm1);
-      const double d1 = P * (LPm1 - z * LP) / (1.0 - z * z);
-      const double d2 = (2.0 * z * d1 - P * (P + 1.0) * LP) / (1.0 - z * z);
-      const double dz = d1 / d2;
-      z -= dz;
-      if (std::fabs(dz) < 1e-16) break;
-    }
-    x[k] = z;
-  }
-  for (int k = 0; k <= P; ++k) {
-    double LP, LPm1;
-    legendre(P, x[k], &LP, &LPm1);
-    w[k] = 2.0 / (P * (P + 1.0) * LP * LP);
-  }
-}
-
-// Closed-form GLL differentiation matrix D[q][a] = l_a'(x_q).
-std::vector<double> gll_diff(int P, const std::vector<double>& x) {
-  std::vector<double> LPv(P + 1);
-  for (int k = 0; k <= P; ++k) {
-    double LPm1;
-    legendre(P, x[k], &LPv[k], &LPm1);
-  }
-  std::vector<double> D((P + 1) * (P + 1), 0.0);
-  for (int q = 0; q <= P; ++q)
-    for (int a = 0; a <= P; ++a) {
-      if (q != a) D[q * (P + 1) + a] = LPv[q] / (LPv[a] * (x[q] - x[a]));
-    }
-  D[0] = -P * (P + 1.0) / 4.0;
-  D[P * (P + 1) + P] = P * (P + 1.0) / 4.0;
-  return D;
-}
 
 std::vector<double> lumped(int n_el, int P, double h, const std::vector<double>& w) {
   std::vector<double> W(n_el * P + 1, 0.0);
@@ -134,15 +77,11 @@ hz_status build_geom(double x0, double x1, double y0, double y1, int nx, int ny,
   g->nlx = snx * P + 1;
   g->nly = sny * P + 1;
   g->NE = g->nlx > g->nly ? g->nlx : g->nly;
-  gll(P, g->xi, g->w);
-  const std::vector<double> D = gll_diff(P, g->xi);
-  g->Kref.assign((P + 1) * (P + 1), 0.0);
-  for (int a = 0; a <= P; ++a)
-    for (int b = 0; b <= P; ++b) {
-      double s = 0.0;
-      for (int q = 0; q <= P; ++q) s += g->w[q] * D[q * (P + 1) + a] * D[q * (P + 1) + b];
-      g->Kref[a * (P + 1) + b] = s;
-    }
+  // the same construction the kernels' compile-time tables come from
+  const gllc::Gll G = gllc::make_gll(P);
+  g->xi.assign(G.x, G.x + P + 1);
+  g->w.assign(G.w, G.w + P + 1);
+  g->Kref.assign(G.K, G.K + (P + 1) * (P + 1));
   g->Wxg = lumped(nx, P, g->hx, g->w);
   g->Wyg = lumped(ny, P, g->hy, g->w);
   g->Wxs = lumped(snx, P, g->hx, g->w);

@@ -92,19 +92,26 @@ struct SweepArgs {
 };
 
 // Parameters of the warp-per-subdomain FP32 sweep (subdomains <= 32 node
-// columns): per-row weights and assembled y-stiffness rows, indexed by
-// compile-time row numbers in the kernel (constant-bank operands).
+// columns).  The assembled y-stiffness rows divided by the row weight are
+// compile-time tables (hz_gll_const.h) times sy = 4/hy^2.
 constexpr int kWarpMaxRows = 33;
 struct WarpSweepArgs {
   SweepArgs base;
   int L;
+  float sy;                                    // 4 / hy^2
   float wyr[kWarpMaxRows];                     // hy/2 * (w_a [own element] + w_P [element below])
-  float kyr[kWarpMaxRows][2 * kMaxP + 1];      // assembled 1D y-stiffness row (taps -P..P) x (2/hy) / Wy_row
 };
 // Register-resident sweep with h warps per subdomain (1, 2 or 4).  Returns
 // HZ_ERR_UNSUPPORTED (without launching) when no variant for (P, sub_ny, h)
 // was compiled or the subdomain has more than 32 node columns.
 hz_status launch_sweep_warp(int P, int sy, int h, const WarpSweepArgs& a, cudaStream_t st);
+
+// Packed sweep of several problems in one launch (register-resident body, one
+// warp per subdomain).  descs: per-problem parameters in device memory;
+// items: {descriptor index, subdomain, shape id, 1 if a source is swept}.
+// packed_shape_id returns -1 when (P, sub_ny, nlx) has no packed variant.
+int packed_shape_id(int P, int sny, int nlx);
+hz_status launch_sweep_packed(const WarpSweepArgs* descs, const int4* items, int nitems, cudaStream_t st);
 
 // FP32 sweep of one subdomain per thread-block cluster (column bands, halo
 // exchange through distributed shared memory).  HZ_ERR_UNSUPPORTED when no

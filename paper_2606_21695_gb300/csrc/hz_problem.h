@@ -8,6 +8,8 @@
 
 namespace hz {
 
+class Packer;
+
 // Owning pinned host buffer (for the small device-to-host reads of the outer loop).
 struct HostBuf {
   void* ptr = nullptr;
@@ -34,6 +36,8 @@ struct hz_problem_s {
   long long sweeps_launched = 0;
   int last_variant = 0;       // sweep kernel used by the last sweep (kVariant*)
   bool autotune = false;      // use / fill the tuned kernel choice for this shape
+  hz::Packer* packer = nullptr;    // set while the solve's sweeps go out in packed launches
+  cudaEvent_t pack_ready = nullptr;  // marks the stream position of a packed sweep request
   // fields (global node grid)
   hz::DevBuf c, f, gb;
   // 1D weight tables
@@ -52,7 +56,7 @@ struct hz_problem_s {
 
 namespace hz {
 using Problem = hz_problem_s;
-constexpr int kVariantAuto = 0, kVariantBlock = 1, kVariantWarp = 2, kVariantCluster = 3;
+constexpr int kVariantAuto = 0, kVariantBlock = 1, kVariantWarp = 2, kVariantCluster = 3, kVariantPacked = 4;
 int sweep_variant();
 struct Choice {
   int variant;  // kVariantBlock / kVariantWarp / kVariantCluster

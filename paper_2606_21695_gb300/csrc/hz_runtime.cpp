@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "hz_internal.h"
+#include "hz_pack.h"
 #include "hz_problem.h"
 
 namespace hz {
@@ -189,21 +190,14 @@ int sweep_variant() {
   return kVariantAuto;
 }
 
-// Row weights and assembled y-stiffness rows of a subdomain for the warp kernel.
+// Row weights of a subdomain and the y scale for the register-resident kernels.
 void warp_rows(const Geom& g, WarpSweepArgs* w) {
   const int P = g.P;
+  w->sy = (float)(4.0 / (g.hy * g.hy));
   for (int j = 0; j < kWarpMaxRows; ++j) {
     const int ay = j % P, ey = j / P;
     const bool own = ey < g.sny, below = ay == 0 && ey >= 1;
     w->wyr[j] = (float)(g.hy / 2.0 * ((own ? g.w[ay] : 0.0) + (below ? g.w[P] : 0.0)));
-    for (int t = -P; t <= P; ++t) {
-      double v = 0.0;
-      if (own && ay + t >= 0 && ay + t <= P) v += g.Kref[ay * (P + 1) + ay + t];
-      if (below && t <= 0) v += g.Kref[P * (P + 1) + P + t];
-      // divided by the row's lumped weight: the kernels use beta' = beta Wx Wy
-      const double wy = g.hy / 2.0 * ((own ? g.w[ay] : 0.0) + (below ? g.w[P] : 0.0));
-      w->kyr[j][t + P] = wy > 0.0 ? (float)(v * (2.0 / g.hy) / wy) : 0.f;
-    }
   }
 }
 
@@ -384,6 +378,22 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
     e1 = pr.events[pr.ev_used + 1];
     pr.ev_used += 2;
     HZ_CUDA(cudaEventRecord(e0, st));
+  }
+  // A solve running as a member of a packer hands its sweep over: one packed
+  // launch per outer step covers the subdomains of every member.
+  if (pr.packer && precision == HZ_FP32_REFINE && !(wh_tol > 0.0)) {
+    const int shape = packed_shape_id(g.P, g.sny, g.nlx);
+    if (shape >= 0) {
+      WarpSweepArgs w{};
+      w.base = a;
+      w.L = g.L;
+      warp_rows(g, &w);
+      HZ_TRY(pr.packer->submit(pr, w, shape, st));
+      pr.last_variant = kVariantPacked;
+      if (e1) HZ_CUDA(cudaEventRecord(e1, st));
+      pr.sweeps_launched++;
+      return HZ_OK;
+    }
   }
   // Kernel choice: HZ_SWEEP_VARIANT forces a variant; otherwise the tuned
   // choice for this shape (if autotuning ran) or the size heuristic:
@@ -885,6 +895,7 @@ void hz_default_opts(hz_solve_opts* o) {
   o->inner_tol = 1e-2;
   o->max_refine = 20;
   o->autotune = 1;
+  o->pack = 1;
 }
 
 hz_status hz_last_error(char* buf, size_t n) {
@@ -1007,6 +1018,7 @@ void hz_problem_destroy(hz_problem pr) {
   cudaSetDevice(pr->device);
   for (cudaEvent_t e : pr->events) cudaEventDestroy(e);
   for (cudaEvent_t e : pr->gm_events) cudaEventDestroy(e);
+  if (pr->pack_ready) cudaEventDestroy(pr->pack_ready);
   if (pr->stream) cudaStreamDestroy(pr->stream);
   delete pr;
 }
@@ -1070,6 +1082,48 @@ hz_status hz_sweep(hz_problem pr, int32_t precision, int32_t nt, int32_t wh_iter
     HZ_TRY(use_device(*pr));
     return sweep(*pr, precision, nt, wh_iters, wh_tol, lam_in, lam_out, rhs_dev, u_sub,
                  static_cast<cudaStream_t>(stream));
+  });
+}
+
+hz_status hz_sweep_packed(const hz_problem* problems, int32_t count, const int32_t* nts, int32_t wh_iters,
+                          const double* const* lam_in, double* const* lam_out, const double* const* rhs,
+                          double* const* u_sub, void* stream) {
+  if (!problems || count < 0 || !nts || !lam_in || !lam_out) return fail(HZ_ERR_INVALID_ARG, "null argument");
+  if (wh_iters < 0) return fail(HZ_ERR_INVALID_ARG, "wh_iters must be >= 0");
+  if (count == 0) return HZ_OK;
+  return guard([&]() -> hz_status {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    HZ_CUDA(cudaGetDevice(&dev));
+    std::vector<WarpSweepArgs> descs(count);
+    std::vector<int4> items;
+    for (int k = 0; k < count; ++k) {
+      if (!problems[k] || !lam_in[k] || !lam_out[k]) return fail(HZ_ERR_INVALID_ARG, "null problem or buffer");
+      if (lam_in[k] == lam_out[k]) return fail(HZ_ERR_INVALID_ARG, "lam_in and lam_out must not alias");
+      Problem& pr = *problems[k];
+      if (pr.device != dev) return fail(HZ_ERR_INVALID_ARG, "problem not on the current device");
+      const Geom& g = pr.g;
+      const int shape = packed_shape_id(g.P, g.sny, g.nlx);
+      if (shape < 0) return fail(HZ_ERR_UNSUPPORTED, "subdomain shape has no packed sweep variant");
+      HZ_TRY(check_ready(pr));
+      HZ_TRY(prepare(pr, nts[k], st));
+      HZ_TRY(ensure_flags(pr));
+      const double* rk = rhs ? rhs[k] : nullptr;
+      double* uk = u_sub ? u_sub[k] : nullptr;
+      descs[k].base = make_sweep_args(pr, true, nts[k], wh_iters, 0.0, lam_in[k], lam_out[k], rk, uk);
+      descs[k].L = g.L;
+      warp_rows(g, &descs[k]);
+      for (int l = 0; l < g.L; ++l) items.push_back(make_int4(k, l, shape, rk ? 1 : 0));
+    }
+    DevBuf dd, di;
+    HZ_TRY(dd.ensure(descs.size() * sizeof(WarpSweepArgs)));
+    HZ_TRY(di.ensure(items.size() * sizeof(int4)));
+    HZ_CUDA(cudaMemcpyAsync(dd.ptr, descs.data(), descs.size() * sizeof(WarpSweepArgs), cudaMemcpyHostToDevice, st));
+    HZ_CUDA(cudaMemcpyAsync(di.ptr, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    HZ_TRY(launch_sweep_packed(dd.as<WarpSweepArgs>(), di.as<int4>(), (int)items.size(), st));
+    HZ_CUDA(cudaStreamSynchronize(st));  // the tables are freed on return
+    for (int k = 0; k < count; ++k) problems[k]->last_variant = kVariantPacked;
+    return HZ_OK;
   });
 }
 

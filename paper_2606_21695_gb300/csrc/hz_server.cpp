@@ -3,9 +3,11 @@
 // submit() snapshots the problem (device-to-device copies of its fields) and
 // queues it.  A pool of worker threads admits queued requests in arrival
 // order whenever the request's estimated device footprint fits in the HBM
-// budget; each admitted solve runs on its own CUDA stream, so the sweeps of
-// all admitted solves overlap on the GPU, and a request that arrives while
-// others run is admitted as soon as a worker and memory free up.  Latency is
+// budget; each admitted solve runs on its own CUDA stream, and with
+// opts.pack the sweeps of all admitted solves go out together, one packed
+// launch per outer step (hz_pack.cpp), so a request that arrives while others
+// run is admitted as soon as a worker and memory free up and joins the next
+// packed launch.  Latency is
 // measured from submit() to the completed device-to-host copy of u.
 #include <cuda_runtime.h>
 
@@ -22,6 +24,7 @@
 #include <vector>
 
 #include "hz_internal.h"
+#include "hz_pack.h"
 #include "hz_problem.h"
 
 using namespace hz;
@@ -97,6 +100,7 @@ struct hz_server_s {
   std::vector<std::thread> workers;
   std::vector<double> latencies_ms;
   uint64_t completed = 0;
+  std::unique_ptr<Packer> packer;  // sweeps of concurrently served solves, one launch per step
   clk::time_point t_start = clk::now();
 
   void worker_loop() {
@@ -118,7 +122,16 @@ struct hz_server_s {
       const size_t nb = (size_t)pr.g.n * 2 * sizeof(double);
       hz_status s = pr.uvec.ensure(nb);
       hz_solve_report rep{};
+      const bool packed = job->opts.pack && packer && Packer::packable(pr, job->opts);
+      if (packed) {
+        pr.packer = packer.get();
+        packer->join();
+      }
       if (s == HZ_OK) s = hz::solve(pr, job->opts, pr.uvec.as<double>(), &rep, pr.stream);
+      if (packed) {
+        packer->leave();
+        pr.packer = nullptr;
+      }
       std::vector<double> u;
       if (s == HZ_OK || s == HZ_ERR_NOT_CONVERGED) {
         u.resize((size_t)pr.g.n * 2);
@@ -137,6 +150,8 @@ struct hz_server_s {
       pr.events.clear();
       for (cudaEvent_t e : pr.gm_events) cudaEventDestroy(e);
       pr.gm_events.clear();
+      if (pr.pack_ready) cudaEventDestroy(pr.pack_ready);
+      pr.pack_ready = nullptr;
       if (pr.stream) cudaStreamDestroy(pr.stream);
       pr.stream = nullptr;
       job->pr.reset();
@@ -168,8 +183,10 @@ hz_status hz_server_create(int32_t device, uint64_t hbm_budget_bytes, hz_server*
     auto* s = new hz_server_s();
     s->device = device;
     s->budget = hbm_budget_bytes;
+    HZ_CUDA(cudaSetDevice(device));
+    s->packer = std::make_unique<Packer>(device);
     const char* env = std::getenv("HZ_SERVER_WORKERS");
-    int nw = env ? std::atoi(env) : 4;
+    int nw = env ? std::atoi(env) : 8;
     nw = std::max(1, std::min(nw, 32));
     for (int k = 0; k < nw; ++k) s->workers.emplace_back([s] { s->worker_loop(); });
     *out = s;

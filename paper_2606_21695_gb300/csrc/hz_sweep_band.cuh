@@ -2,7 +2,8 @@
 //
 // Same arithmetic as the warp-per-subdomain kernel (hz_sweep_warp.cuh):
 // lane i owns node column i (at most 32 columns), the x part of A p comes
-// from neighbour lanes by shuffles, the y part from rows held in registers.
+// from neighbour lanes by shuffles (hz_sweep_xrow.cuh), the y part from rows
+// held in registers.
 // The NY = SY*P+1 rows are split into H bands of consecutive rows, one warp
 // each, so a subdomain's state is spread over H warps: fewer registers per
 // thread and H times more warps per SM to hide latency.  Each time step a
@@ -41,7 +42,6 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
   constexpr int J0 = B * S::RB;
   constexpr int J1 = (B + 1) * S::RB < NY ? (B + 1) * S::RB : NY;
   constexpr int NR = J1 - J0;
-  constexpr int NK = 2 * P + 1;
   static_assert(NR >= P, "every band must hold at least P rows");
   constexpr bool HAS_LO = B > 0, HAS_HI = B < H - 1;
   const SweepArgs& a = x.base;
@@ -58,16 +58,11 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
   // with beta' = beta Wx Wy the stiffness terms are divided by the lumped
   // weights: (A p)/(Wx Wy) = (Kx p)/Wx + (Ky p)/Wy
   const double wx_lane = a.hx2 * ((own_x ? a.w[ax] : 0.0) + (left_x ? a.w[P] : 0.0));
-  float kx[NK];
-#pragma unroll
-  for (int tt = 0; tt < NK; ++tt) {
-    const int off = tt - P;
-    double v = 0.0;
-    const int b = ax + off;
-    if (own_x && b >= 0 && b <= P) v += a.Kref[ax * (P + 1) + b];
-    if (left_x && off <= 0) v += a.Kref[P * (P + 1) + (off + P)];
-    kx[tt] = live ? (float)(v * a.kxs / wx_lane) : 0.f;
-  }
+  XRow<P> xr;
+  xr.init(lane, nlx, a.sxe, a.Kref, a.kxs, [&](int c) {
+    const int ac = c % P, ec_ = c / P;
+    return a.hx2 * ((ec_ < a.sxe ? a.w[ac] : 0.0) + (ac == 0 && ec_ >= 1 ? a.w[P] : 0.0));
+  });
 
   // ---- node data of the band's rows (edge data as in the warp kernel)
   const int64_t nn = (int64_t)nlx * NY;
@@ -109,8 +104,7 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
     }
     if (j == 0 || j == NY - 1) { alE = al; bEr = SRC ? 0.f : fbr; bEi = SRC ? 0.f : fbi; }
     if (j > 0 && j < NY - 1) {
-      if (slot < 2) ecg[j * 3 + slot] = make_float4(al, SRC ? 0.f : fbr, SRC ? 0.f : fbi, 0.f);
-      if (lane == 2 || (nlx <= 2 && lane == 31)) ecg[j * 3 + 2] = make_float4(1.f, 0.f, 0.f, 0.f);
+      if (slot < 2) ecg[j * 2 + slot] = make_float4(al - 1.f, SRC ? 0.f : fbr, SRC ? 0.f : fbi, 0.f);
     }
   }
   __syncwarp();
@@ -118,6 +112,7 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
   const float4* tab = static_cast<const float4*>(a.tab);
   const float sigma = (float)a.sigma, omega = (float)a.omega;
   const float cpi = (float)a.cpi, spi = (float)a.spi, scale = (float)a.two_over_nt;
+  const float sy = x.sy;
   // exchange buffer layout: [parity][band][side 0 = first P rows, 1 = last P rows][P][32]
   auto xb = [&](int par, int band, int side, int k) -> float& {
     return xbuf[(((par * H + band) * 2 + side) * P + k) * 32 + lane];
@@ -166,29 +161,23 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         const int j = J0 + r;
-        // (A p)_j / (Wx Wy): y taps (registers and halo rows), then x taps by shuffles
-        float Ap = kx[P] * p[r];
+        // (A p)_j / (Wx Wy): y taps (registers and halo rows, compile-time
+        // coefficients times 4/hy^2), x part by shuffles
+        float Y = 0.f;
 #pragma unroll
         for (int t = -P; t <= P; ++t) {
           const int jj = j + t;
           if (warp_sweep::tap(P, SY, j, t) && jj >= 0 && jj < NY) {
             const float v = (jj < J0) ? lo[jj - (J0 - P)] : (jj >= J1) ? hi[jj - J1] : p[jj - J0];
-            Ap += x.kyr[j][t + P] * v;
+            Y += kYRows.c[P - 1][gllc::row_class(P, SY, j)][t + P] * v;
           }
         }
-#pragma unroll
-        for (int t = 1; t <= P; ++t) {
-          const float up = __shfl_down_sync(0xffffffffu, p[r], t);  // lane i+t
-          const float dn = __shfl_up_sync(0xffffffffu, p[r], t);    // lane i-t
-          Ap += kx[P + t] * up;
-          Ap += kx[P - t] * dn;
-        }
+        const float Ap = xr.apply(p[r], lane) + sy * Y;
         float f;
         if (j == 0 || j == NY - 1) {
           f = alE * pd[r] - bet[r] * Ap + bEr * tb.x + bEi * tb.y;
         } else {
-          const float4 e = ecg[j * 3 + slot];
-          f = e.x * pd[r] - bet[r] * Ap + e.y * tb.x + e.z * tb.y;
+          f = edge_fix(pd[r] - bet[r] * Ap, pd[r], &ecg[j * 2 + (slot & 1)], slot < 2, tb.x, tb.y);
         }
         if (SRC) f += bbr[r] * tb.x + bbi[r] * tb.y;
         pd[r] = f;
@@ -303,7 +292,7 @@ __global__ void __launch_bounds__(H * 32, 7) sweep_band_kernel(const __grid_cons
   using S = Shape<P, SY, H>;
   constexpr int NY = S::NY;
   __shared__ float xbuf_all[S::G][2 * H * 2 * P * 32];
-  __shared__ float4 ec_all[S::G][NY * 3];
+  __shared__ float4 ec_all[S::G][NY * 2];
   __shared__ float2 uold_all[H][S::RB * 32];
   __shared__ double red_all[S::G][2 * H];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -2,12 +2,12 @@
 // columns and NY = SY*P+1 rows: lane i owns node column i, every row of it
 // in registers for the whole WaveHoltz loop (p, p-dot, v, alpha, beta,
 // beta*b).  The time step needs no shared memory and no barrier:
-//   x part of A p: assembled 1D row (2P+1 taps, per-lane coefficients in
-//                  registers) against neighbour lanes via warp shuffles;
-//   y part:        assembled 1D rows whose sparsity pattern is fixed at
-//                  compile time (row j's position in its element and the
-//                  subdomain ends), coefficients are kernel parameters, so
-//                  they are constant-bank operands of the FMAs.
+//   x part of A p: assembled 1D row, own-element neighbours gathered by P
+//                  indexed shuffles plus one hand-off for the element to the
+//                  left (hz_sweep_xrow.cuh), per-lane coefficients in registers;
+//   y part:        assembled 1D rows whose sparsity pattern and values
+//                  (in units of 4/hy^2) are fixed at compile time by row j's
+//                  class (hz_gll_const.h), constant-bank operands of the FMAs.
 // Same arithmetic as the block sweep (Algorithm 1, modified leapfrog and
 // eq. (WaveHoltz) with the -1/(i omega) sign and 2/N_t scaling; lambda
 // update -lambda - 2ik u); several subdomains per block, one per warp.
@@ -15,14 +15,12 @@
 
 #include <cuda_runtime.h>
 
+#include "hz_gll_const.h"
 #include "hz_internal.h"
+#include "hz_sweep_xrow.cuh"
 
 namespace hz {
 namespace warp_sweep {
-
-// One subdomain per block: 1024 subdomains spread as 6-7 blocks per SM over
-// 152 SMs, instead of whole 4-subdomain blocks landing unevenly.
-constexpr int kWarpsPerBlock = 1;
 
 // Is tap t of assembled 1D row j structurally non-zero?  Row j lies in
 // element j/P at position j%P; class-0 rows also touch the element below.
@@ -34,16 +32,17 @@ __host__ __device__ constexpr bool tap(int P, int ne, int j, int t) {
   return own || below;
 }
 
-template <int P, int SY, bool SRC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) sweep_warp_kernel(const __grid_constant__ WarpSweepArgs x) {
+// Sweep of subdomain l by the calling warp.  x may live in the parameter
+// space (one problem per launch) or in global memory (packed launches).
+// ec: per-warp shared table of the edge columns' rows; uo: per-warp shared
+// stash of the previous iterate, used only when STASH and a WaveHoltz
+// tolerance is set (may be null otherwise).
+template <int P, int SY, bool SRC, bool STASH>
+__device__ __forceinline__ void warp_body(const WarpSweepArgs& x, int l, float4 (*ec)[2], float2* uo) {
   constexpr int NY = SY * P + 1;
-  constexpr int NK = 2 * P + 1;
   constexpr int NB = SRC ? NY : 1;  // per-node forcing only when a source is present
   const SweepArgs& a = x.base;
   const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int l = blockIdx.x * kWarpsPerBlock + wib;
-  if (l >= x.L) return;  // whole warp leaves together
   const int sxi = l % a.Sx, syi = l / a.Sx;
   const int nlx = a.nlx;
   const int i = lane;
@@ -56,25 +55,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) sweep_warp_kernel(const _
   // with beta' = beta Wx Wy the stiffness terms are divided by the lumped
   // weights: (A p)/(Wx Wy) = (Kx p)/Wx + (Ky p)/Wy, so no weight multiplies remain
   const double wx_lane = a.hx2 * ((own_x ? a.w[ax] : 0.0) + (left_x ? a.w[P] : 0.0));
-  float kx[NK];
-#pragma unroll
-  for (int tt = 0; tt < NK; ++tt) {
-    const int off = tt - P;
-    double v = 0.0;
-    const int b = ax + off;
-    if (own_x && b >= 0 && b <= P) v += a.Kref[ax * (P + 1) + b];
-    if (left_x && off <= 0) v += a.Kref[P * (P + 1) + (off + P)];
-    kx[tt] = live ? (float)(v * a.kxs / wx_lane) : 0.f;
-  }
+  XRow<P> xr;
+  xr.init(lane, nlx, a.sxe, a.Kref, a.kxs, [&](int c) {
+    const int ac = c % P, ec_ = c / P;
+    return a.hx2 * ((ec_ < a.sxe ? a.w[ac] : 0.0) + (ac == 0 && ec_ >= 1 ? a.w[P] : 0.0));
+  });
 
   // ---- node coefficients and right-hand side.  alpha != 1 and (without a
   // source) b != 0 only on the subdomain edges: rows 0 and NY-1 keep them in
-  // registers, the edge columns' interior rows in a shared table read with
-  // one broadcast load per row (slot 2 is the interior value {1, 0, 0}).
-  __shared__ float4 ecol[kWarpsPerBlock][NY][3];
-  __shared__ float2 uold[kWarpsPerBlock][NY][32];
-  float4(&ec)[NY][3] = ecol[wib];
-  float2(&uo)[NY][32] = uold[wib];
+  // registers, the edge columns' interior rows in a shared table (alpha - 1,
+  // beta b) that only the two edge lanes read.
   const int64_t nn = (int64_t)nlx * NY;
   const float* betaG = static_cast<const float*>(a.beta) + (int64_t)l * nn;
   const float* alphaG = static_cast<const float*>(a.alpha) + (int64_t)l * nn;
@@ -113,8 +103,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) sweep_warp_kernel(const _
     if (j == 0) { al0 = (float)al; b0r = SRC ? 0.f : fbr; b0i = SRC ? 0.f : fbi; }
     if (j == NY - 1) { alN = (float)al; bNr = SRC ? 0.f : fbr; bNi = SRC ? 0.f : fbi; }
     if (j > 0 && j < NY - 1) {
-      if (slot < 2) ec[j][slot] = make_float4((float)al, SRC ? 0.f : fbr, SRC ? 0.f : fbi, 0.f);
-      if (lane == 2 || (nlx <= 2 && lane == 31)) ec[j][2] = make_float4(1.f, 0.f, 0.f, 0.f);
+      if (slot < 2) ec[j][slot] = make_float4((float)(al - 1.0), SRC ? 0.f : fbr, SRC ? 0.f : fbi, 0.f);
     }
   }
   __syncwarp();
@@ -122,6 +111,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) sweep_warp_kernel(const _
   const float4* tab = static_cast<const float4*>(a.tab);
   const float sigma = (float)a.sigma, omega = (float)a.omega;
   const float cpi = (float)a.cpi, spi = (float)a.spi, scale = (float)a.two_over_nt;
+  const float sy = x.sy;
+  const int Nt = a.Nt, m_wh = a.m_wh;
+  const bool tol = STASH && a.wh_tol > 0.0;
+  const double wh_tol = a.wh_tol;
   // between WaveHoltz iterations u lives in (vre, vim); the previous iterate
   // is kept in shared memory only when a tolerance is checked
   float p[NY], pd[NY], vre[NY], vim[NY];
@@ -129,10 +122,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) sweep_warp_kernel(const _
   for (int j = 0; j < NY; ++j) { vre[j] = 0.f; vim[j] = 0.f; }
 
   int m_done = 0;
-  for (int m = 0; m < a.m_wh; ++m) {
-    if (a.wh_tol > 0.0) {
+  for (int m = 0; m < m_wh; ++m) {
+    if (tol) {
 #pragma unroll
-      for (int j = 0; j < NY; ++j) uo[j][lane] = make_float2(vre[j], vim[j]);
+      for (int j = 0; j < NY; ++j) uo[j * 32 + lane] = make_float2(vre[j], vim[j]);
     }
     {
       const float4 t0 = tab[0];
@@ -145,34 +138,29 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) sweep_warp_kernel(const _
       }
     }
     float4 tb = tab[1];
-    for (int nu = 1; nu < a.Nt; ++nu) {
+    for (int nu = 1; nu < Nt; ++nu) {
       const float4 tn = tab[nu + 1];  // prefetch (the table has N_t + 1 entries)
 #pragma unroll
       for (int j = 0; j < NY; ++j) p[j] += sigma * pd[j];
 #pragma unroll
       for (int j = 0; j < NY; ++j) {
-        // (A p)_j / (Wx Wy): y taps from registers (compile-time sparsity,
-        // coefficients in the constant bank), then x taps from neighbour lanes
-        float Ap = kx[P] * p[j];
+        // (A p)_j / (Wx Wy): y taps from registers (compile-time sparsity and
+        // coefficients, constant-bank operands) times 4/hy^2, x part from
+        // neighbour lanes
+        float Y = 0.f;
 #pragma unroll
         for (int t = -P; t <= P; ++t) {
-          if (tap(P, SY, j, t) && j + t >= 0 && j + t < NY) Ap += x.kyr[j][t + P] * p[j + t];
+          if (tap(P, SY, j, t) && j + t >= 0 && j + t < NY)
+            Y += kYRows.c[P - 1][gllc::row_class(P, SY, j)][t + P] * p[j + t];
         }
-#pragma unroll
-        for (int t = 1; t <= P; ++t) {
-          const float up = __shfl_down_sync(0xffffffffu, p[j], t);  // lane i+t
-          const float dn = __shfl_up_sync(0xffffffffu, p[j], t);    // lane i-t
-          Ap += kx[P + t] * up;
-          Ap += kx[P - t] * dn;
-        }
+        const float Ap = xr.apply(p[j], lane) + sy * Y;
         float f;
         if (j == 0) {
           f = al0 * pd[j] - bet[j] * Ap + b0r * tb.x + b0i * tb.y;
         } else if (j == NY - 1) {
           f = alN * pd[j] - bet[j] * Ap + bNr * tb.x + bNi * tb.y;
         } else {
-          const float4 e = ec[j][slot];
-          f = e.x * pd[j] - bet[j] * Ap + e.y * tb.x + e.z * tb.y;
+          f = edge_fix(pd[j] - bet[j] * Ap, pd[j], &ec[j][slot & 1], slot < 2, tb.x, tb.y);
         }
         if (SRC) f += bbr[j] * tb.x + bbi[j] * tb.y;
         pd[j] = f;
@@ -190,11 +178,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) sweep_warp_kernel(const _
       vim[j] *= scale;
     }
     m_done = m + 1;
-    if (a.wh_tol > 0.0) {
+    if (tol) {
       double dn = 0.0, un = 0.0;
 #pragma unroll
       for (int j = 0; j < NY; ++j) {
-        const float2 o = uo[j][lane];
+        const float2 o = uo[j * 32 + lane];
         const double dr = (double)vre[j] - (double)o.x, di = (double)vim[j] - (double)o.y;
         dn += dr * dr + di * di;
         un += (double)vre[j] * vre[j] + (double)vim[j] * vim[j];
@@ -204,7 +192,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) sweep_warp_kernel(const _
         dn += __shfl_xor_sync(0xffffffffu, dn, o);
         un += __shfl_xor_sync(0xffffffffu, un, o);
       }
-      if (dn <= a.wh_tol * a.wh_tol * un) break;  // warp-uniform after the reduction
+      if (dn <= wh_tol * wh_tol * un) break;  // warp-uniform after the reduction
     }
   }
 
@@ -271,6 +259,18 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) sweep_warp_kernel(const _
       put(1, t, false, 0.0, 0.0);
     }
   }
+}
+
+// One subdomain (one warp) per block: 1024 subdomains spread as 6-7 blocks
+// per SM over 152 SMs, instead of multi-warp blocks landing unevenly.
+template <int P, int SY, bool SRC>
+__global__ void __launch_bounds__(32) sweep_warp_kernel(const __grid_constant__ WarpSweepArgs x) {
+  constexpr int NY = SY * P + 1;
+  __shared__ float4 ec[NY][2];
+  __shared__ float2 uo[NY * 32];
+  const int l = blockIdx.x;
+  if (l >= x.L) return;
+  warp_body<P, SY, SRC, true>(x, l, ec, uo);
 }
 
 }  // namespace warp_sweep

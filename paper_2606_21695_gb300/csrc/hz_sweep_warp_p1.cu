@@ -10,9 +10,9 @@ namespace {
 template <int P, int SY, int H>
 hz_status launch(const WarpSweepArgs& a, cudaStream_t st) {
   if constexpr (H == 1) {
-    const int blocks = (a.L + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    if (a.base.rhs) sweep_warp_kernel<P, SY, true><<<blocks, kWarpsPerBlock * 32, 0, st>>>(a);
-    else sweep_warp_kernel<P, SY, false><<<blocks, kWarpsPerBlock * 32, 0, st>>>(a);
+    const int blocks = a.L;  // one subdomain (one warp) per block
+    if (a.base.rhs) sweep_warp_kernel<P, SY, true><<<blocks, 32, 0, st>>>(a);
+    else sweep_warp_kernel<P, SY, false><<<blocks, 32, 0, st>>>(a);
   } else {
     const int blocks = a.L;  // one subdomain (H warps) per block
     if (a.base.rhs) band_sweep::sweep_band_kernel<P, SY, true, H><<<blocks, H * 32, 0, st>>>(a);

@@ -1,0 +1,81 @@
+// x part of the assembled stiffness apply for the register-resident sweeps
+// (lane i owns node column i of a subdomain with at most 32 columns).
+//
+// (Kx p)_i / Wx_i with Kx the assembled 1D stiffness (Sec. 4: sum over the
+// elements containing node i of the element matrix 2/hx Kref):
+//   own element e = i / P (nodes eP .. eP+P, lane i is its node a = i % P):
+//       sum_b Kref[a][b] p_{eP+b}
+//   element e-1, only for a = 0 (lane i is that element's node P):
+//       sum_b Kref[P][b] p_{(e-1)P+b}
+// A lane gathers the P other nodes of its own element by indexed shuffles
+// and contracts them with its row.  The element-(e-1) part of lane eP is
+// formed by lane eP-1, which holds all of element e-1 after its own gather,
+// and handed over by one more shuffle; its b = P term (lane eP's own value)
+// stays in lane eP's centre coefficient.  P+1 shuffles per row instead of
+// the 2P of a centred (2P+1)-tap stencil, for one extra FMA.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace hz {
+
+template <int P>
+struct XRow {
+  int src[P + 1];    // src[k]: lane holding own-element node (a + k) mod (P+1), k = 1..P
+  float kown[P + 1];  // kown[k]: coefficient of that node (k = 0: the lane itself)
+  float kl[P + 1];    // kl[k]: element-(e-1) coefficient for the right neighbour (k = 1 unused)
+
+  // Kref: (P+1)^2 reference stiffness (row a), kxs = 2/hx, wx(i) = lumped
+  // 1D weight of column i; columns >= nlx are dead (all coefficients 0).
+  template <typename WX>
+  __device__ __forceinline__ void init(int lane, int nlx, int sxe, const double* Kref, double kxs, WX wx) {
+    const int a = lane % P, e = lane / P;
+    const bool live = lane < nlx;
+    const bool own = live && e < sxe;
+    const bool left = live && a == 0 && e >= 1;
+    const double s_me = live ? kxs / wx(lane) : 0.0;
+    // the right neighbour receives kl-part iff it is an element's first node
+    // with an element to its left (a + 1 == P) and exists
+    const bool sends = live && (a == P - 1) && (lane + 1 < nlx);
+    const double s_nb = sends ? kxs / wx(lane + 1) : 0.0;
+    for (int k = 0; k <= P; ++k) {
+      const int b = (a + k) % (P + 1);
+      src[k] = (e * P + b) & 31;
+      double v = 0.0;
+      if (own) v += Kref[a * (P + 1) + b];
+      if (k == 0 && left) v += Kref[P * (P + 1) + P];  // lane is node P of element e-1
+      kown[k] = (float)(v * s_me);
+      // element e-1 of the neighbour is this lane's own element: row P
+      kl[k] = (sends && k != 1) ? (float)(Kref[P * (P + 1) + b] * s_nb) : 0.f;
+    }
+  }
+
+  // Returns (Kx p)_i / Wx_i for the row value pj of this lane.
+  __device__ __forceinline__ float apply(float pj, int lane) const {
+    float own = kown[0] * pj;
+    float lp = kl[0] * pj;
+#pragma unroll
+    for (int k = 1; k <= P; ++k) {
+      const float v = __shfl_sync(0xffffffffu, pj, src[k]);
+      own += kown[k] * v;
+      if (k != 1) lp += kl[k] * v;
+    }
+    // lane 0 reads lane 31, whose part is 0 (dead, or the last column)
+    return own + __shfl_sync(0xffffffffu, lp, (lane + 31) & 31);
+  }
+};
+
+// Edge-column correction of the p-dot update of a row.  The interior update
+// is f = p-dot - beta' A p; the two edge lanes add (alpha - 1) p-dot +
+// beta b_re cos + beta b_im sin with (alpha - 1, beta b_re, beta b_im) read
+// from shared memory.  Only the edge lanes load (no shared-memory traffic
+// for interior lanes) and no per-row default values are needed.
+__device__ __forceinline__ float edge_fix(float f, float pd, const float4* row, bool edge, float c, float s) {
+  if (edge) {
+    const float4 e = *row;
+    f += e.x * pd + e.y * c + e.z * s;
+  }
+  return f;
+}
+
+}  // namespace hz

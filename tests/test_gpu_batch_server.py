@@ -1,6 +1,7 @@
 """Batched solves and the request server: every result equals the same
 problem solved alone (bitwise: fixed reduction orders, kernel choice cached
-per shape), admission against the HBM budget, error paths."""
+per shape, and a packed sweep's arithmetic per subdomain does not depend on
+what else is in the launch), admission against the HBM budget, error paths."""
 
 import time
 
@@ -22,11 +23,13 @@ def _mix():
     ]
 
 
-def _opts(hz):
-    return hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=1e-8)
+def _opts(hz, pack=1):
+    return hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=1e-8, pack=pack)
 
 
 def test_batch_equals_individual_solves(hz):
+    """Unpacked batch: each solve launches its own (autotuned) sweeps, so
+    the results equal the solo solves bitwise."""
     from paper_2606_21695_gb300.api import Case
 
     cases = [Case(wl) for wl in _mix()]
@@ -36,20 +39,54 @@ def test_batch_equals_individual_solves(hz):
         assert st == hz.HZ_OK, rep
         assert rep["sweep_variant"] in (1, 2, 3)
         solo.append(u.copy())
-    st, sts, us, reps = hz.hz_solve_batch([c.pr for c in cases], [c.n for c in cases], _opts(hz), max_concurrent=4)
+    st, sts, us, reps = hz.hz_solve_batch([c.pr for c in cases], [c.n for c in cases], _opts(hz, pack=0),
+                                          max_concurrent=4)
     assert st == hz.HZ_OK and all(s == hz.HZ_OK for s in sts)
     for k in range(len(cases)):
         assert reps[k]["rel_residual"] <= 1e-8
         assert np.array_equal(us[k], solo[k]), k
 
 
+def test_packed_batch_same_alone_and_in_mix(hz):
+    """Packed batch: one launch per outer step sweeps every member; a
+    problem's result is bitwise the same batched alone or with the others,
+    and within the solve tolerance of the unpacked solve."""
+    from paper_2606_21695_gb300.api import Case
+
+    cases = [Case(wl) for wl in _mix()]
+    packable = [0, 1, 3]  # (P, sub_ny) = (2, 4), (3, 4), (2, 8); mixC has (4, 8): unpacked
+    alone = []
+    for c in cases:
+        st, sts, us, reps = hz.hz_solve_batch([c.pr], [c.n], _opts(hz))
+        assert st == hz.HZ_OK
+        alone.append((us[0].copy(), reps[0]))
+    for k, (u, rep) in enumerate(alone):
+        assert rep["rel_residual"] <= 1e-8
+        assert rep["sweep_variant"] == 4 if k in packable else rep["sweep_variant"] in (1, 2, 3)
+    for order in ([0, 1, 2, 3], [3, 2, 1, 0]):
+        sub = [cases[k] for k in order]
+        st, sts, us, reps = hz.hz_solve_batch([c.pr for c in sub], [c.n for c in sub], _opts(hz))
+        assert st == hz.HZ_OK and all(s == hz.HZ_OK for s in sts)
+        for i, k in enumerate(order):
+            assert np.array_equal(us[i], alone[k][0]), k
+            assert reps[i]["sweeps"] == alone[k][1]["sweeps"]
+    for k in packable:
+        st, u, rep = hz.hz_solve(cases[k].pr, _opts(hz), n=cases[k].n)
+        # both solves stop at a relative residual of 1e-8
+        assert np.max(np.abs(alone[k][0] - u)) <= 1e-5 * np.max(np.abs(u))
+
+
 def test_server_results_same_alone_and_in_mix(hz):
     from paper_2606_21695_gb300.api import Case
 
     cases = [Case(wl) for wl in _mix()]
-    solo = [hz.hz_solve(c.pr, _opts(hz), n=c.n)[1].copy() for c in cases]
     srv = hz.hz_server_create(0, 8 << 30)
     try:
+        solo = []
+        for c in cases:  # each request served alone
+            done, st, u, rep = hz.hz_server_poll(srv, hz.hz_server_submit(srv, c.pr, _opts(hz)), -1, n=c.n)
+            assert done and st == hz.HZ_OK and rep["rel_residual"] <= 1e-8
+            solo.append(u.copy())
         tickets = []
         for rnd in range(2):  # requests arrive while others run
             for c in cases:
