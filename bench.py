@@ -437,6 +437,57 @@ def _cheap_cfg4(k):
     return [w for _, w in rows[:k]]
 
 
+# (degree, subdomain elements in y) compiled into the packed sweep; the
+# subdomain must also have at most 32 node columns
+PACKED_SHAPES = {(1, 4), (1, 8), (1, 16), (2, 4), (2, 8), (3, 4), (3, 8), (4, 4), (5, 4)}
+
+
+def _packable(w):
+    return (w.P, w.sub_ny) in PACKED_SHAPES and w.sub_nx * w.P + 1 <= 32
+
+
+def _cheap_packable_cfg4(k):
+    return [w for w in _cheap_cfg4(64) if _packable(w)][:k]
+
+
+def _batch_group(hz, cases, max_sweeps):
+    """Sequential solves (with and without the step graphs), an unpacked
+    concurrent batch and a packed batch of the same problems."""
+    import torch
+
+    prs, ns = [c.pr for c in cases], [c.n for c in cases]
+    mk = lambda **kw: hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, max_sweeps=max_sweeps, **kw)
+    opts, popts, nog = mk(pack=0), mk(pack=1), mk(pack=0, graphs=0)
+    hz.hz_solve_batch(prs, ns, opts, 8, want_u=False)  # warm-up / autotune / graph capture
+    hz.hz_solve_batch(prs, ns, popts, 0, want_u=False)
+    torch.cuda.synchronize()
+    out = {}
+    t0 = time.perf_counter()
+    seq = [hz.hz_solve(c.pr, nog, n=c.n) for c in cases]
+    out["sequential_nographs_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    seq = [hz.hz_solve(c.pr, opts, n=c.n) for c in cases]
+    out["sequential_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    st, sts, _, reps = hz.hz_solve_batch(prs, ns, opts, 8, want_u=False)
+    out["batched_s"] = time.perf_counter() - t0
+    k0 = hz.hz_kernel_launches()
+    t0 = time.perf_counter()
+    pst, psts, _, preps = hz.hz_solve_batch(prs, ns, popts, 0, want_u=False)
+    out["packed_s"] = time.perf_counter() - t0
+    out["packed_kernel_launches"] = hz.hz_kernel_launches() - k0
+    out["packed_members"] = sum(r["sweep_variant"] == 4 for r in preps)
+    out["speedup_batched"] = out["sequential_s"] / out["batched_s"]
+    out["speedup_packed"] = out["sequential_s"] / out["packed_s"]
+    out["dof_updates_per_s_batched"] = sum(r["dof_updates"] for r in reps) / out["batched_s"]
+    out["dof_updates_per_s_packed"] = sum(r["dof_updates"] for r in preps) / out["packed_s"]
+    out["solves_per_s_packed"] = len(cases) / out["packed_s"]
+    out["max_rel_residual"] = max(r["rel_residual"] for r in reps + preps + [s[2] for s in seq])
+    out["statuses"] = [hz.STATUS_NAMES[s] for s in sts]
+    out["packed_statuses"] = [hz.STATUS_NAMES[s] for s in psts]
+    return out
+
+
 def run_batch(args):
     """--mode batch: the cheapest problems of the batched workload solved one
     at a time and together (hz_solve_batch); FP32 sweeps + FP64 refinement."""
@@ -447,34 +498,17 @@ def run_batch(args):
 
     wls = _cheap_cfg4(args.batch)
     cases = [Case(w) for w in wls]
-    opts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, max_sweeps=5000, pack=0)
-    popts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, max_sweeps=5000, pack=1)
-    prs, ns = [c.pr for c in cases], [c.n for c in cases]
-    hz.hz_solve_batch(prs, ns, opts, 8, want_u=False)  # warm-up / autotune
-    hz.hz_solve_batch(prs, ns, popts, 0, want_u=False)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    seq = [hz.hz_solve(c.pr, opts, n=c.n) for c in cases]
-    t_seq = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    st, sts, _, reps = hz.hz_solve_batch(prs, ns, opts, 8, want_u=False)
-    t_bat = time.perf_counter() - t0
-    k0 = hz.hz_kernel_launches()
-    t0 = time.perf_counter()
-    pst, psts, _, preps = hz.hz_solve_batch(prs, ns, popts, 0, want_u=False)
-    t_pack = time.perf_counter() - t0
-    k_pack = hz.hz_kernel_launches() - k0
-    dof = sum(r["dof_updates"] for r in reps)
-    pdof = sum(r["dof_updates"] for r in preps)
-    return {"mode": "batch", "problems": [w.name for w in wls], "solves": len(cases),
-            "sequential_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat,
-            "solves_per_s_batched": len(cases) / t_bat, "dof_updates_per_s_batched": dof / t_bat,
-            "packed_s": t_pack, "packed_speedup": t_seq / t_pack, "solves_per_s_packed": len(cases) / t_pack,
-            "dof_updates_per_s_packed": pdof / t_pack, "packed_members": sum(r["sweep_variant"] == 4 for r in preps),
-            "packed_kernel_launches": k_pack,
-            "max_rel_residual": max(r["rel_residual"] for r in reps + preps),
-            "statuses": [hz.STATUS_NAMES[s] for s in sts], "packed_statuses": [hz.STATUS_NAMES[s] for s in psts],
-            "sequential_residual_max": max(s[2]["rel_residual"] for s in seq)}
+    res = {"mode": "batch", "problems": [w.name for w in wls], "solves": len(cases),
+           "cheapest": _batch_group(hz, cases, 5000)}
+    for c in cases:
+        c.close()
+    pw = _cheap_packable_cfg4(min(args.batch, 10))
+    pcases = [Case(w) for w in pw]
+    res["packable_problems"] = [w.name for w in pw]
+    res["cheapest_packable"] = _batch_group(hz, pcases, 5000)
+    for c in pcases:
+        c.close()
+    return res
 
 
 def run_serve(args):

@@ -111,6 +111,10 @@ typedef struct {
                             subdomain of every member (FP32 sweeps with a fixed WaveHoltz count
                             on subdomains of at most 32 node columns and degree 1..5; other
                             solves run unpacked).  Ignored by hz_solve. */
+  int32_t graphs;        /* 1: the vector work of each GMRES (Arnoldi) step -- Gram-Schmidt dots and
+                            updates, norm, normalisation, read-back of the Hessenberg column -- is
+                            captured once per step index as a CUDA graph and replayed in later
+                            cycles (one launch instead of about ten per step) */
 } hz_solve_opts;
 
 typedef struct {
@@ -128,7 +132,8 @@ typedef struct {
 } hz_solve_report;
 
 /* Defaults: FP64, tol 1e-8, 2000 sweeps, GMRES(60), 20 WaveHoltz iterations,
- * no wh_tol, CFL 0.9, inner_tol 1e-2, 20 refinements, autotune on, pack on. */
+ * no wh_tol, CFL 0.9, inner_tol 1e-2, 20 refinements, autotune, pack and
+ * graphs on. */
 HZ_API void hz_default_opts(hz_solve_opts* opts);
 
 /* Copies the calling thread's last error message (NUL-terminated, truncated

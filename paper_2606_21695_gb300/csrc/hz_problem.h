@@ -48,6 +48,11 @@ struct hz_problem_s {
   hz::DevBuf bvec, rvec, uvec, usub, gv, xv, tv, V, part, small, flags, hcol;
   hz::HostBuf hsmall, hcol_host;
   std::vector<cudaEvent_t> gm_events;  // one per Arnoldi step of a cycle
+  // CUDA graphs of the Arnoldi step's vector work, one per step index of the
+  // GMRES cycle, valid while step_graph_key (buffers, sizes) is unchanged
+  std::vector<cudaGraphExec_t> step_graphs;
+  std::vector<long long> step_graph_kernels;
+  std::vector<const void*> step_graph_key;
   // per-sweep CUDA events while a solve runs (report.sweep_seconds)
   bool time_sweeps = false;
   size_t ev_used = 0;
@@ -76,4 +81,7 @@ hz_status rhs(Problem& pr, double* b, cudaStream_t st);
 hz_status assemble_add(Problem& pr, const double* u_sub, double* u, cudaStream_t st);
 hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report* rep, cudaStream_t st);
 hz_status check_ready(const Problem& pr);
+void release_step_graphs(Problem& pr);
+unsigned long long launch_count();
+void add_launches(long long n);
 }  // namespace hz

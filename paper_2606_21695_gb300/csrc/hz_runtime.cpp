@@ -9,6 +9,7 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -27,6 +28,8 @@ thread_local std::string g_last_error;
 std::atomic<unsigned long long> g_launches{0};
 }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void add_launches(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 void set_error(const std::string& msg) { g_last_error = msg; }
 hz_status fail(hz_status s, const std::string& msg) {
   set_error(msg);
@@ -105,6 +108,14 @@ static GlobalArgs global_args(const Problem& pr) {
   a.Wxg = pr.Wxg.as<double>();
   a.Wyg = pr.Wyg.as<double>();
   return a;
+}
+
+void release_step_graphs(Problem& pr) {
+  for (cudaGraphExec_t g : pr.step_graphs)
+    if (g) cudaGraphExecDestroy(g);
+  pr.step_graphs.clear();
+  pr.step_graph_kernels.clear();
+  pr.step_graph_key.clear();
 }
 
 hz_status check_ready(const Problem& pr) {
@@ -342,6 +353,9 @@ hz_status autotune(Problem& pr, int precision, int nt, int m_wh, cudaStream_t st
     cudaEventSynchronize(e1);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
+    if (std::getenv("HZ_TUNE_LOG"))
+      std::fprintf(stderr, "hz autotune %s: candidate %d/%d %.4f ms per sweep\n", key.c_str(), cand.variant, cand.ty,
+                   ms / 2);
     if (ms < best) {
       best = ms;
       bc = cand;
@@ -351,6 +365,8 @@ hz_status autotune(Problem& pr, int precision, int nt, int m_wh, cudaStream_t st
   cudaEventDestroy(e1);
   HZ_CUDA(cudaGetLastError());
   store_choice(key, bc);
+  if (std::getenv("HZ_TUNE_LOG"))
+    std::fprintf(stderr, "hz autotune %s: variant %d/%d, %.4f ms per sweep\n", key.c_str(), bc.variant, bc.ty, best / 2);
   return HZ_OK;
 }
 
@@ -601,11 +617,11 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
         }
         double* hd = pr.hcol.as<double>();
         double* hh = pr.hcol_host.as<double>();
-        auto enqueue = [&](int j) -> hz_status {
+        // the step's vector work after its sweep (a fixed sequence of launches
+        // for a given j: captured as a CUDA graph with opts.graphs)
+        auto post = [&](int j) -> hz_status {
           double* vj = V + (size_t)j * n2;
           double* w = V + (size_t)(j + 1) * n2;
-          hz_status s = do_sweep(c, vj, tv, nullptr, nullptr);
-          if (s != HZ_OK) return s;
           HZ_CUDA(cudaMemcpyAsync(w, vj, vb, cudaMemcpyDeviceToDevice, c.st));
           HZ_TRY(launch_axpby(-1.0, tv, 1.0, w, n2, c.st));  // w = v_j - S v_j
           const int nv = j + 1;
@@ -620,7 +636,56 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
           double* hslot = hh + (size_t)j * (CS + 4);
           HZ_CUDA(cudaMemcpyAsync(hslot, col, CS * sizeof(double), cudaMemcpyDeviceToHost, c.st));
           HZ_CUDA(cudaMemcpyAsync(hslot + CS, pr.flags.ptr, 16, cudaMemcpyDeviceToHost, c.st));
-          HZ_CUDA(cudaEventRecord(pr.gm_events[j], c.st));
+          // while a graph is captured the record must be external to become an
+          // event node the host can wait on
+          cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+          HZ_CUDA(cudaStreamIsCapturing(c.st, &cap));
+          if (cap == cudaStreamCaptureStatusActive)
+            HZ_CUDA(cudaEventRecordWithFlags(pr.gm_events[j], c.st, cudaEventRecordExternal));
+          else
+            HZ_CUDA(cudaEventRecord(pr.gm_events[j], c.st));
+          return HZ_OK;
+        };
+        if (c.o.graphs) {
+          // every buffer the captured work touches exists before the capture
+          HZ_TRY(pr.part.ensure((size_t)vec_blocks(n2) * (m + 1) * 2 * sizeof(double) + 64));
+          const std::vector<const void*> key = {V, tv, hd, hh, pr.flags.ptr, pr.part.ptr, (const void*)(intptr_t)n2,
+                                                (const void*)(intptr_t)m, (const void*)(intptr_t)real};
+          if (key != pr.step_graph_key) {
+            release_step_graphs(pr);
+            pr.step_graph_key = key;
+          }
+          if ((int)pr.step_graphs.size() < m) {
+            pr.step_graphs.resize(m, nullptr);
+            pr.step_graph_kernels.resize(m, 0);
+          }
+        }
+        auto enqueue = [&](int j) -> hz_status {
+          hz_status s = do_sweep(c, V + (size_t)j * n2, tv, nullptr, nullptr);
+          if (s != HZ_OK) return s;
+          if (!c.o.graphs) return post(j);
+          if (!pr.step_graphs[j]) {
+            const unsigned long long k0 = launch_count();
+            HZ_CUDA(cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal));
+            const hz_status ps = post(j);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(c.st, &graph);
+            const long long kn = (long long)(launch_count() - k0);
+            add_launches(-kn);  // counted when the graph runs
+            if (ps != HZ_OK || ce != cudaSuccess) {
+              if (graph) cudaGraphDestroy(graph);
+              (void)cudaGetLastError();
+              return ps != HZ_OK ? ps : cuda_fail(ce, "capture of the Arnoldi step");
+            }
+            cudaGraphExec_t ex = nullptr;
+            const cudaError_t ie = cudaGraphInstantiate(&ex, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate");
+            pr.step_graphs[j] = ex;
+            pr.step_graph_kernels[j] = kn;
+          }
+          HZ_CUDA(cudaGraphLaunch(pr.step_graphs[j], c.st));
+          add_launches(pr.step_graph_kernels[j]);
           return HZ_OK;
         };
         hz_status es = enqueue(0);
@@ -896,6 +961,7 @@ void hz_default_opts(hz_solve_opts* o) {
   o->max_refine = 20;
   o->autotune = 1;
   o->pack = 1;
+  o->graphs = 1;
 }
 
 hz_status hz_last_error(char* buf, size_t n) {
@@ -1018,6 +1084,7 @@ void hz_problem_destroy(hz_problem pr) {
   cudaSetDevice(pr->device);
   for (cudaEvent_t e : pr->events) cudaEventDestroy(e);
   for (cudaEvent_t e : pr->gm_events) cudaEventDestroy(e);
+  release_step_graphs(*pr);
   if (pr->pack_ready) cudaEventDestroy(pr->pack_ready);
   if (pr->stream) cudaStreamDestroy(pr->stream);
   delete pr;

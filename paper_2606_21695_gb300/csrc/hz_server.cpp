@@ -152,6 +152,7 @@ struct hz_server_s {
       pr.gm_events.clear();
       if (pr.pack_ready) cudaEventDestroy(pr.pack_ready);
       pr.pack_ready = nullptr;
+      release_step_graphs(pr);
       if (pr.stream) cudaStreamDestroy(pr.stream);
       pr.stream = nullptr;
       job->pr.reset();
