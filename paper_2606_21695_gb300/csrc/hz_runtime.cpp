@@ -250,7 +250,9 @@ hz_status launch_choice(Problem& pr, const SweepArgs& a0, Choice c, bool fp32, c
     s = launch_sweep_warp(g.P, g.sny, c.ty > 0 ? c.ty : 1, w, st);
   } else if (c.variant == kVariantCluster) {
     if (!fp32) return HZ_ERR_UNSUPPORTED;
-    s = launch_sweep_cluster(g.P, a0, g.L, st);
+    SweepArgs a = a0;
+    a.ty_force = c.ty;  // 4: 4P rows per thread, else 2P
+    s = launch_sweep_cluster(g.P, a, g.L, st);
   } else {
     SweepArgs a = a0;
     a.ty_force = c.ty;
@@ -332,7 +334,7 @@ hz_status autotune(Problem& pr, int precision, int nt, int m_wh, cudaStream_t st
   std::vector<Choice> cands;
   if (fp32)
     cands = {{kVariantWarp, 1}, {kVariantWarp, 2}, {kVariantWarp, 4}, {kVariantBlock, 1}, {kVariantBlock, 2},
-             {kVariantCluster, 0}};
+             {kVariantCluster, 0}, {kVariantCluster, 4}};
   else cands = {{kVariantBlock, 1}, {kVariantBlock, 2}};
   cudaEvent_t e0, e1;
   HZ_CUDA(cudaEventCreate(&e0));
@@ -437,7 +439,9 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
   const bool small_block = (int64_t)g.nlx * ((g.nly + g.P - 1) / g.P) <= 256;
   if (ls == HZ_ERR_UNSUPPORTED && fp32 &&
       (want == kVariantCluster || (want == kVariantAuto && !small_block))) {
-    ls = launch_choice(pr, a, Choice{kVariantCluster, 0}, fp32, st);
+    // HZ_CLUSTER_TY=4 forces 4P rows per thread in the cluster kernel (tests)
+    const char* cty = std::getenv("HZ_CLUSTER_TY");
+    ls = launch_choice(pr, a, Choice{kVariantCluster, cty ? std::atoi(cty) : 0}, fp32, st);
     if (ls != HZ_OK && ls != HZ_ERR_UNSUPPORTED) return ls;
     if (ls != HZ_OK && want == kVariantCluster) return fail(HZ_ERR_UNSUPPORTED, "no cluster sweep shape fits");
   }

@@ -26,10 +26,20 @@ namespace hz {
 namespace cluster_sweep {
 namespace {
 
-constexpr int kMaxThreads = 512;
+// Threads per CTA at most: 512 with 2P rows per thread (TY = 2, up to 128
+// registers), 256 with 4P rows (TY = 4, up to 255 registers).
+template <int TY>
+struct ClusterBlock {
+  static constexpr int kMaxThreads = TY >= 4 ? 256 : 512;
+};
 
-template <int P, int TY, int CN>
-__global__ void __launch_bounds__(kMaxThreads) sweep_cluster_kernel(const __grid_constant__ SweepArgs a, int BW) {
+// SRC: the sweep carries a source (every node forced); without it, alpha != 1
+// and the forcing live only on the subdomain's edges, kept out of the
+// per-thread registers: the first and last node rows in six registers, the
+// edge columns' other rows in a shared table read by the edge threads only.
+template <int P, int TY, int CN, bool SRC>
+__global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_kernel(const __grid_constant__ SweepArgs a,
+                                                                                   int BW) {
   constexpr int RY = P * TY;
   constexpr int NK = 2 * P + 1;
   cg::cluster_group cluster = cg::this_cluster();
@@ -56,6 +66,9 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_cluster_kernel(const __grid
   float* buf0 = sm;
   float* buf1 = sm + PS;
   float2* stash = reinterpret_cast<float2*>(sm + 2 * PS);  // previous iterate (tolerance mode)
+  // edge-column table (no source): row j of this band's W (slot 0) / E (slot 1) column,
+  // at a 16-byte aligned offset after the tiles and the stash
+  float4* ecol = reinterpret_cast<float4*>(sm + ((2 * PS + 2 * nly * BW + 3) & ~3));
 
   for (int k = t; k < 2 * PS; k += blockDim.x) sm[k] = 0.f;
   float* left0 = q > 0 ? cluster.map_shared_rank(buf0, q - 1) : nullptr;
@@ -100,7 +113,12 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_cluster_kernel(const __grid
   const float* alphaG = static_cast<const float*>(a.alpha) + (int64_t)l * nn;
   const double* lamL = a.lam_in + (int64_t)l * 4 * a.NE * 2;
   const bool ifW = sxi > 0, ifE = sxi < a.Sx - 1, ifS = syi > 0, ifN = syi < a.Sy - 1;
-  float bet[RY], alp[RY], bbr[RY], bbi[RY];
+  constexpr int NR = SRC ? RY : 1;
+  float bet[RY], alp[NR], bbr[NR], bbi[NR];
+  // no source: first / last node row of the subdomain (all columns), and the edge columns
+  float al0 = 1.f, b0r = 0.f, b0i = 0.f, alN = 1.f, bNr = 0.f, bNi = 0.f;
+  const int slot = (i == 0) ? 0 : (i == nlx - 1) ? 1 : 2;
+  const bool edge_col = active && slot < 2;
 #pragma unroll
   for (int r = 0; r < RY; ++r) {
     const int j = j0 + r;
@@ -110,7 +128,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_cluster_kernel(const __grid
       const int64_t n = (int64_t)j * nlx + i;
       be = (double)betaG[n];
       al = (double)alphaG[n];
-      if (a.rhs) {
+      if (SRC) {
         const double shx = ((i == 0 && ifW) || (i == nlx - 1 && ifE)) ? 0.5 : 1.0;
         const double shy = ((j == 0 && ifS) || (j == nly - 1 && ifN)) ? 0.5 : 1.0;
         const int64_t I = (int64_t)sxi * a.snxP + i, J = (int64_t)syi * a.snyP + j;
@@ -124,9 +142,16 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_cluster_kernel(const __grid
       if (j == nly - 1 && ifN) { br += a.wxs[i] * lamL[2 * (3 * a.NE + i)]; bi += a.wxs[i] * lamL[2 * (3 * a.NE + i) + 1]; }
     }
     bet[r] = (float)be;
-    alp[r] = (float)al;
-    bbr[r] = (float)(be * br);
-    bbi[r] = (float)(be * bi);
+    if (SRC) {
+      alp[r] = (float)al;
+      bbr[r] = (float)(be * br);
+      bbi[r] = (float)(be * bi);
+    } else if (live) {
+      if (j == 0) { al0 = (float)al; b0r = (float)(be * br); b0i = (float)(be * bi); }
+      if (j == nly - 1) { alN = (float)al; bNr = (float)(be * br); bNi = (float)(be * bi); }
+      if (j > 0 && j < nly - 1 && slot < 2)
+        ecol[j * 2 + slot] = make_float4((float)(al - 1.0), (float)(be * br), (float)(be * bi), 0.f);
+    }
   }
 
   const float4* tab = static_cast<const float4*>(a.tab);
@@ -217,7 +242,21 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_cluster_kernel(const __grid
           sx += kx[tt] * row[tt];
         }
         const float Ap = wy[r] * sx + wxy * sy[r];
-        pd[r] = alp[r] * pd[r] - bet[r] * Ap + bbr[r] * tb.x + bbi[r] * tb.y;
+        if (SRC) {
+          pd[r] = alp[r] * pd[r] - bet[r] * Ap + bbr[r] * tb.x + bbi[r] * tb.y;
+        } else {
+          const int j = j0 + r;
+          float f = pd[r] - bet[r] * Ap;
+          if (r % P == 0) {  // only element-boundary rows can be the first or last row
+            if (j == 0) f += (al0 - 1.f) * pd[r] + b0r * tb.x + b0i * tb.y;
+            if (j == nly - 1) f += (alN - 1.f) * pd[r] + bNr * tb.x + bNi * tb.y;
+          }
+          if (edge_col && j > 0 && j < nly - 1) {
+            const float4 e = ecol[j * 2 + slot];
+            f += e.x * pd[r] + e.y * tb.x + e.z * tb.y;
+          }
+          pd[r] = f;
+        }
         vre[r] += tb.z * p[r];
         vim[r] += tb.w * pd[r];
       }
@@ -338,12 +377,13 @@ template <int P, int TY, int CN>
 hz_status launch(SweepArgs a, int L, int BW, cudaStream_t st) {
   constexpr int RY = P * TY;
   const int threads = ((BW * a.NS + 31) / 32) * 32;
-  if (threads > kMaxThreads) return HZ_ERR_UNSUPPORTED;
+  if (threads > ClusterBlock<TY>::kMaxThreads) return HZ_ERR_UNSUPPORTED;
   const int rowsP = a.NS * RY + P + 1;
   const int colsP = BW + 2 * P;
-  size_t smem = (size_t)2 * rowsP * colsP * sizeof(float) + (size_t)2 * a.nly * BW * sizeof(float);
+  const size_t edge_off = (size_t)((2 * rowsP * colsP + 2 * a.nly * BW + 3) & ~3);  // floats, as in the kernel
+  size_t smem = edge_off * sizeof(float) + (size_t)2 * a.nly * sizeof(float4);
   if (smem > 220 * 1024) return HZ_ERR_UNSUPPORTED;
-  auto kern = sweep_cluster_kernel<P, TY, CN>;
+  auto kern = a.rhs ? sweep_cluster_kernel<P, TY, CN, true> : sweep_cluster_kernel<P, TY, CN, false>;
   HZ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(L * CN));
@@ -362,19 +402,27 @@ hz_status launch(SweepArgs a, int L, int BW, cudaStream_t st) {
   return HZ_OK;
 }
 
-template <int P>
-hz_status launch_P(SweepArgs a, int L, cudaStream_t st) {
-  // smallest cluster whose bands fit in one block of <= 512 threads (TY = 2)
-  a.NS = (a.nly + 2 * P - 1) / (2 * P);
+template <int P, int TY>
+hz_status launch_TY(SweepArgs a, int L, cudaStream_t st) {
+  // smallest cluster whose bands fit in one block
+  a.NS = (a.nly + TY * P - 1) / (TY * P);
   for (int cn : {2, 4, 8}) {
     const int BW = (a.nlx + cn - 1) / cn;
     if (BW * (cn - 1) >= a.nlx || BW < P) continue;  // every band non-empty, halos within one band
-    if (((BW * a.NS + 31) / 32) * 32 > kMaxThreads) continue;
-    if (cn == 2) return launch<P, 2, 2>(a, L, BW, st);
-    if (cn == 4) return launch<P, 2, 4>(a, L, BW, st);
-    return launch<P, 2, 8>(a, L, BW, st);
+    if (((BW * a.NS + 31) / 32) * 32 > ClusterBlock<TY>::kMaxThreads) continue;
+    if (cn == 2) return launch<P, TY, 2>(a, L, BW, st);
+    if (cn == 4) return launch<P, TY, 4>(a, L, BW, st);
+    return launch<P, TY, 8>(a, L, BW, st);
   }
   return HZ_ERR_UNSUPPORTED;
+}
+
+// Rows per thread 2P (a.ty_force != 4) or 4P (a.ty_force == 4, fewer and
+// fuller threads: more work between cluster barriers).
+template <int P>
+hz_status launch_P(SweepArgs a, int L, cudaStream_t st) {
+  if (a.ty_force == 4) return launch_TY<P, 4>(a, L, st);
+  return launch_TY<P, 2>(a, L, st);
 }
 
 }  // namespace

@@ -368,11 +368,14 @@ CLUSTER_LAYOUTS = [
 ]
 
 
+@pytest.mark.parametrize("ty", ["2", "4"])
 @pytest.mark.parametrize("nx,ny,sx,sy,P", CLUSTER_LAYOUTS)
-def test_sweep_fp32_cluster_matches_oracle(hz, monkeypatch, nx, ny, sx, sy, P):
+def test_sweep_fp32_cluster_matches_oracle(hz, monkeypatch, nx, ny, sx, sy, P, ty):
     """Subdomain split over a thread-block cluster (halo pushed through
-    distributed shared memory), forced on shapes that also fit one block."""
+    distributed shared memory), forced on shapes that also fit one block;
+    2P or 4P node rows per thread."""
     monkeypatch.setenv("HZ_SWEEP_VARIANT", "cluster")
+    monkeypatch.setenv("HZ_CLUSTER_TY", ty)
     wl = _wl(nx, ny, sx, sy, P)
     case, pr = _pair(hz, wl, g_seed=nx + P)
     nt = hz.hz_problem_nt(case.pr)
