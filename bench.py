@@ -35,6 +35,10 @@ if ROOT not in sys.path:
 METRIC = "DOF-updates/s"
 UNIT = "DOF-updates/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
+# DRAM bytes (read + write) of one launch of the one-warp-per-subdomain sweep
+# on the 256x256, P=3 workload, from one ncu capture of this kernel version
+# (coefficients and lambda read once; independent of the WaveHoltz count)
+SWEEP_WARP_TRAFFIC_BYTES = 7.632896e6
 TOL = 1e-8
 
 
@@ -332,11 +336,17 @@ def run_ours(args):
                       "sweep_kernel": {1: "block", 2: "warp", 3: "cluster"}.get(reports[0]["sweep_variant"]),
                       "refinements": reports[0]["refinements"], "gmres_iters": reports[0]["gmres_iters"],
                       "dof_updates_per_solve": dof / args.steps},
-            "roofline": {"kernel": {1: "sweep_kernel (block)", 2: "sweep_warp_kernel / sweep_band_kernel",
+            "roofline": {"kernel": {1: "sweep_kernel (block)",
+                                    2: ("sweep_warp_kernel (one warp per subdomain)" if reports[0]["sweep_shape"] <= 1
+                                        else f"sweep_band_kernel ({reports[0]['sweep_shape']} warps per subdomain)"),
                                     3: "sweep_cluster_kernel"}.get(reports[0]["sweep_variant"], "?")
                          + " FP32, one launch = one DD sweep", "bound": "alu",
                          "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "frac": achieved / FP32_PEAK_TFLOPS,
+                         "traffic": SWEEP_WARP_TRAFFIC_BYTES if (wl.P == 3 and reports[0]["sweep_variant"] == 2
+                                                                 and reports[0]["sweep_shape"] == 1) else None,
+                         "traffic_unit": "bytes per launch (DRAM, ncu)",
+                         "sweep_shape": reports[0]["sweep_shape"],
                          "algorithmic": f"{flops_per_update} flop/DOF-update x {dof_per_launch:.4g} DOF-updates/launch",
                          "avg_launch_ms": avg_launch * 1e3, "launch_share": sweep_s / elapsed},
             "cpu_baseline": cpu,

@@ -45,7 +45,8 @@ class hz_solve_opts(C.Structure):
 class hz_solve_report(C.Structure):
     _fields_ = [("sweeps", C.c_int32), ("refinements", C.c_int32), ("nt", C.c_int32), ("wh_iters_max", C.c_int32),
                 ("rel_residual", C.c_double), ("seconds", C.c_double), ("dof_updates", C.c_int64),
-                ("gmres_iters", C.c_int32), ("sweep_variant", C.c_int32), ("sweep_seconds", C.c_double)]
+                ("gmres_iters", C.c_int32), ("sweep_variant", C.c_int32), ("sweep_shape", C.c_int32),
+                ("sweep_seconds", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

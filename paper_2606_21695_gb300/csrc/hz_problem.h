@@ -35,6 +35,7 @@ struct hz_problem_s {
   int prepared_nt = 0, prepared_version = -1;
   long long sweeps_launched = 0;
   int last_variant = 0;       // sweep kernel used by the last sweep (kVariant*)
+  int last_shape = 0;         // and its Choice::ty
   bool autotune = false;      // use / fill the tuned kernel choice for this shape
   hz::Packer* packer = nullptr;    // set while the solve's sweeps go out in packed launches
   cudaEvent_t pack_ready = nullptr;  // marks the stream position of a packed sweep request

@@ -258,7 +258,10 @@ hz_status launch_choice(Problem& pr, const SweepArgs& a0, Choice c, bool fp32, c
     a.ty_force = c.ty;
     s = launch_sweep(fp32, g.P, a, g.L, st);
   }
-  if (s == HZ_OK) pr.last_variant = c.variant;
+  if (s == HZ_OK) {
+    pr.last_variant = c.variant;
+    pr.last_shape = c.variant == kVariantWarp ? (c.ty > 0 ? c.ty : 1) : c.ty;
+  }
   return s;
 }
 
@@ -408,6 +411,7 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
       warp_rows(g, &w);
       HZ_TRY(pr.packer->submit(pr, w, shape, st));
       pr.last_variant = kVariantPacked;
+      pr.last_shape = 1;
       if (e1) HZ_CUDA(cudaEventRecord(e1, st));
       pr.sweeps_launched++;
       return HZ_OK;
@@ -847,6 +851,7 @@ hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report*
   (void)cudaGetLastError();
   rep.sweep_seconds = sw;
   rep.sweep_variant = pr.last_variant;
+  rep.sweep_shape = pr.last_shape;
   pr.time_sweeps = false;
   rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (rep_out) *rep_out = rep;
