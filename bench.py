@@ -151,10 +151,12 @@ def oracle_sample(wl, seconds, nsub_max=1024):
     lam = np.zeros((m.L, 4, m.NE), complex)
     ctx = threadpool_limits(1) if threadpool_limits else None
     try:
-        # calibrate on 2 subdomains, then size the sample to ~seconds
+        # calibrate on a few subdomains (the oracle is vectorised over them, so
+        # fewer would overstate the per-subdomain cost), then size the sample
+        ncal = min(16, m.L)
         t0 = time.perf_counter()
-        pr.sweep(lam, rhs, nt, 1, subset=[0, 1])
-        t_cal = (time.perf_counter() - t0) / (2 * 1)
+        pr.sweep(lam, rhs, nt, 1, subset=list(range(ncal)))
+        t_cal = (time.perf_counter() - t0) / ncal
         nsub = int(max(1, min(nsub_max, seconds / max(t_cal * m_wh, 1e-6))))
         subset = list(range(0, m.L, max(1, m.L // nsub)))[:nsub]
         t0 = time.perf_counter()

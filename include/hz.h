@@ -185,7 +185,9 @@ HZ_API hz_status hz_problem_nt(hz_problem pr, double cfl, int32_t* nt);
  * Returns HZ_ERR_NOT_CONVERGED (report filled, u_out written) if the budget
  * runs out, HZ_ERR_DIVERGED on non-finite values. */
 HZ_API hz_status hz_solve(hz_problem pr, const hz_solve_opts* opts, double* u_out, hz_solve_report* report);
-/* Same with the solution written to device memory u_out_dev (n complex). */
+/* Same with the solution written to device memory u_out_dev (n complex),
+ * ordered on `stream` (a default stream -- legacy or per-thread -- is joined
+ * by events and the work runs on the problem's own stream). */
 HZ_API hz_status hz_solve_device(hz_problem pr, const hz_solve_opts* opts, double* u_out_dev, hz_solve_report* report,
                           void* stream);
 

@@ -39,6 +39,7 @@ struct hz_problem_s {
   bool autotune = false;      // use / fill the tuned kernel choice for this shape
   hz::Packer* packer = nullptr;    // set while the solve's sweeps go out in packed launches
   cudaEvent_t pack_ready = nullptr;  // marks the stream position of a packed sweep request
+  cudaEvent_t join_event = nullptr;  // orders a solve on the problem's stream with a caller's default stream
   // fields (global node grid)
   hz::DevBuf c, f, gb;
   // 1D weight tables
@@ -83,6 +84,7 @@ hz_status assemble_add(Problem& pr, const double* u_sub, double* u, cudaStream_t
 hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report* rep, cudaStream_t st);
 hz_status check_ready(const Problem& pr);
 void release_step_graphs(Problem& pr);
+bool is_default_stream(cudaStream_t s);
 unsigned long long launch_count();
 void add_launches(long long n);
 }  // namespace hz

@@ -110,6 +110,8 @@ static GlobalArgs global_args(const Problem& pr) {
   return a;
 }
 
+bool is_default_stream(cudaStream_t s) { return s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread; }
+
 void release_step_graphs(Problem& pr) {
   for (cudaGraphExec_t g : pr.step_graphs)
     if (g) cudaGraphExecDestroy(g);
@@ -654,7 +656,8 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
             HZ_CUDA(cudaEventRecord(pr.gm_events[j], c.st));
           return HZ_OK;
         };
-        if (c.o.graphs) {
+        const bool graphs = c.o.graphs && !is_default_stream(c.st);  // default streams cannot be captured
+        if (graphs) {
           // every buffer the captured work touches exists before the capture
           HZ_TRY(pr.part.ensure((size_t)vec_blocks(n2) * (m + 1) * 2 * sizeof(double) + 64));
           const std::vector<const void*> key = {V, tv, hd, hh, pr.flags.ptr, pr.part.ptr, (const void*)(intptr_t)n2,
@@ -671,7 +674,7 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
         auto enqueue = [&](int j) -> hz_status {
           hz_status s = do_sweep(c, V + (size_t)j * n2, tv, nullptr, nullptr);
           if (s != HZ_OK) return s;
-          if (!c.o.graphs) return post(j);
+          if (!graphs) return post(j);
           if (!pr.step_graphs[j]) {
             const unsigned long long k0 = launch_count();
             HZ_CUDA(cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal));
@@ -1095,6 +1098,7 @@ void hz_problem_destroy(hz_problem pr) {
   for (cudaEvent_t e : pr->gm_events) cudaEventDestroy(e);
   release_step_graphs(*pr);
   if (pr->pack_ready) cudaEventDestroy(pr->pack_ready);
+  if (pr->join_event) cudaEventDestroy(pr->join_event);
   if (pr->stream) cudaStreamDestroy(pr->stream);
   delete pr;
 }
@@ -1132,7 +1136,18 @@ hz_status hz_solve_device(hz_problem pr, const hz_solve_opts* opts, double* u_ou
     HZ_TRY(use_device(*pr));
     hz_solve_opts o;
     opts_or_default(opts, &o);
-    return solve(*pr, o, u_out_dev, report, static_cast<cudaStream_t>(stream));
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    if (!is_default_stream(cs)) return solve(*pr, o, u_out_dev, report, cs);
+    // A default stream cannot be captured into the step graphs: run on the
+    // problem's own stream, ordered after the caller's work and before the
+    // caller's later work.
+    if (!pr->join_event) HZ_CUDA(cudaEventCreateWithFlags(&pr->join_event, cudaEventDisableTiming));
+    HZ_CUDA(cudaEventRecord(pr->join_event, cs));
+    HZ_CUDA(cudaStreamWaitEvent(pr->stream, pr->join_event, 0));
+    const hz_status s = solve(*pr, o, u_out_dev, report, pr->stream);
+    HZ_CUDA(cudaEventRecord(pr->join_event, pr->stream));
+    HZ_CUDA(cudaStreamWaitEvent(cs, pr->join_event, 0));
+    return s;
   });
 }
 

@@ -33,3 +33,26 @@ def test_graphs_replay_the_same_launches(hz, outer):
                                                                         r0["refinements"])
         assert k1 == k0
     case.close()
+
+
+def test_device_solve_on_default_and_side_streams(hz):
+    """hz_solve_device on the default stream (joined by events, solved on the
+    problem's stream with the step graphs) and on a side stream give the
+    solution of hz_solve bitwise."""
+    import torch
+
+    from paper_2606_21695_gb300.api import Case
+
+    case = Case(configs.Workload("gs", (0, 1, 0, 1), 16, 16, 2, 4, 4, 11.0, "random", (0.5, 0.4), 0.04,
+                                 corr_len=0.3))
+    o = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=1e-8, gmres_restart=10)
+    st, ref, _ = hz.hz_solve(case.pr, o, n=case.n)
+    assert st == hz.HZ_OK
+    side = torch.cuda.Stream()
+    for stream in (None, torch.cuda.current_stream(), side):
+        u = torch.full((2 * case.n,), float("nan"), dtype=torch.float64, device="cuda")
+        st, rep = hz.hz_solve_device(case.pr, o, u, stream)
+        torch.cuda.synchronize()
+        assert st == hz.HZ_OK
+        assert np.array_equal(u.cpu().numpy().view(np.complex128), ref)
+    case.close()
