@@ -335,13 +335,14 @@ def run_ours(args):
             "time_to_tol_s": {"fp32_refine": elapsed / args.steps, "fp64": fp64["seconds"] if fp64 else None},
             "fp64_solve": fp64,
             "solve": {"sweeps_per_solve": sweeps / args.steps, "rel_residual_max": max(res),
-                      "sweep_kernel": {1: "block", 2: "warp", 3: "cluster"}.get(reports[0]["sweep_variant"]),
+                      "sweep_kernel": {1: "block", 2: "warp", 3: "cluster", 4: "packed",
+                                       5: "cluster of warp bands"}.get(reports[0]["sweep_variant"]),
                       "refinements": reports[0]["refinements"], "gmres_iters": reports[0]["gmres_iters"],
                       "dof_updates_per_solve": dof / args.steps},
             "roofline": {"kernel": {1: "sweep_kernel (block)",
                                     2: ("sweep_warp_kernel (one warp per subdomain)" if reports[0]["sweep_shape"] <= 1
                                         else f"sweep_band_kernel ({reports[0]['sweep_shape']} warps per subdomain)"),
-                                    3: "sweep_cluster_kernel"}.get(reports[0]["sweep_variant"], "?")
+                                    3: "sweep_cluster_kernel", 5: "sweep_cband_kernel"}.get(reports[0]["sweep_variant"], "?")
                          + " FP32, one launch = one DD sweep", "bound": "alu",
                          "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS,

@@ -127,7 +127,7 @@ typedef struct {
   int64_t dof_updates;   /* sum over sweeps of subdomain nodes x (N_t - 1) x WaveHoltz iterations */
   int32_t gmres_iters;   /* total GMRES iterations */
   int32_t sweep_variant; /* kernel of the last sweep: 1 block, 2 warp per subdomain, 3 cluster,
-                            4 packed with other solves */
+                            4 packed with other solves, 5 cluster of warp bands */
   int32_t sweep_shape;   /* its configuration: warps per subdomain (2), rows per thread in units
                             of the degree (1, 3; 0 = chosen by size) */
   double sweep_seconds;  /* device time of the sweep kernels (CUDA events on the solve's stream) */

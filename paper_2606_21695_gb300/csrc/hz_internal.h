@@ -118,6 +118,12 @@ hz_status launch_sweep_packed(const WarpSweepArgs* descs, const int4* items, int
 // cluster shape fits.
 hz_status launch_sweep_cluster(int P, const SweepArgs& a, int L, cudaStream_t st);
 
+// FP32 sweep of subdomains wider than 32 node columns by a cluster of CTAs,
+// one per 32-column band, one warp per row band, state in registers (degree
+// 1, 2 or 4; fixed WaveHoltz count).  HZ_ERR_UNSUPPORTED when no compiled
+// shape fits.
+hz_status launch_sweep_cband(int P, const SweepArgs& a, int L, cudaStream_t st);
+
 // Launches the sweep in Real = float (fp32 = true) or double.  Returns
 // HZ_ERR_UNSUPPORTED when no compiled variant fits the subdomain.
 hz_status launch_sweep_f32(int P, const SweepArgs& a, int L, cudaStream_t st);

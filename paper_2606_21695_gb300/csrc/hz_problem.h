@@ -63,7 +63,8 @@ struct hz_problem_s {
 
 namespace hz {
 using Problem = hz_problem_s;
-constexpr int kVariantAuto = 0, kVariantBlock = 1, kVariantWarp = 2, kVariantCluster = 3, kVariantPacked = 4;
+constexpr int kVariantAuto = 0, kVariantBlock = 1, kVariantWarp = 2, kVariantCluster = 3, kVariantPacked = 4,
+              kVariantClusterBand = 5;
 int sweep_variant();
 struct Choice {
   int variant;  // kVariantBlock / kVariantWarp / kVariantCluster

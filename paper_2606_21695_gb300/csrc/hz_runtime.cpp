@@ -200,6 +200,7 @@ int sweep_variant() {
   if (std::strcmp(v, "block") == 0) return kVariantBlock;
   if (std::strcmp(v, "warp") == 0) return kVariantWarp;
   if (std::strcmp(v, "cluster") == 0) return kVariantCluster;
+  if (std::strcmp(v, "cband") == 0) return kVariantClusterBand;
   return kVariantAuto;
 }
 
@@ -250,6 +251,9 @@ hz_status launch_choice(Problem& pr, const SweepArgs& a0, Choice c, bool fp32, c
     w.L = g.L;
     warp_rows(g, &w);
     s = launch_sweep_warp(g.P, g.sny, c.ty > 0 ? c.ty : 1, w, st);
+  } else if (c.variant == kVariantClusterBand) {
+    if (!fp32) return HZ_ERR_UNSUPPORTED;
+    s = launch_sweep_cband(g.P, a0, g.L, st);
   } else if (c.variant == kVariantCluster) {
     if (!fp32) return HZ_ERR_UNSUPPORTED;
     SweepArgs a = a0;
@@ -339,7 +343,7 @@ hz_status autotune(Problem& pr, int precision, int nt, int m_wh, cudaStream_t st
   std::vector<Choice> cands;
   if (fp32)
     cands = {{kVariantWarp, 1}, {kVariantWarp, 2}, {kVariantWarp, 4}, {kVariantBlock, 1}, {kVariantBlock, 2},
-             {kVariantCluster, 0}, {kVariantCluster, 4}};
+             {kVariantCluster, 0}, {kVariantCluster, 4}, {kVariantClusterBand, 0}};
   else cands = {{kVariantBlock, 1}, {kVariantBlock, 2}};
   cudaEvent_t e0, e1;
   HZ_CUDA(cudaEventCreate(&e0));
@@ -443,6 +447,12 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
     if (ls != HZ_OK && want == kVariantWarp) return fail(HZ_ERR_UNSUPPORTED, "no warp sweep variant for this subdomain");
   }
   const bool small_block = (int64_t)g.nlx * ((g.nly + g.P - 1) / g.P) <= 256;
+  if (ls == HZ_ERR_UNSUPPORTED && fp32 && want == kVariantClusterBand) {  // else only when autotuned
+    ls = launch_choice(pr, a, Choice{kVariantClusterBand, 0}, fp32, st);
+    if (ls != HZ_OK && ls != HZ_ERR_UNSUPPORTED) return ls;
+    if (ls != HZ_OK && want == kVariantClusterBand)
+      return fail(HZ_ERR_UNSUPPORTED, "no cluster-of-bands sweep shape fits");
+  }
   if (ls == HZ_ERR_UNSUPPORTED && fp32 &&
       (want == kVariantCluster || (want == kVariantAuto && !small_block))) {
     // HZ_CLUSTER_TY=4 forces 4P rows per thread in the cluster kernel (tests)

@@ -122,6 +122,10 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
   for (int r = 0; r < NR; ++r) { vre[r] = 0.f; vim[r] = 0.f; }
 
   int m_done = 0;
+  // buffer parity runs on across WaveHoltz iterations: consecutive time steps
+  // always alternate buffers (N_t - 1 may be odd), which the single barrier
+  // per step relies on
+  int cur = 0;
   for (int m = 0; m < a.m_wh; ++m) {
     if (a.wh_tol > 0.0) {
 #pragma unroll
@@ -138,7 +142,6 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
       }
     }
     float4 tb = tab[1];
-    int cur = 0;
     for (int nu = 1; nu < a.Nt; ++nu) {
       const float4 tn = tab[nu + 1];  // prefetch (the table has N_t + 1 entries)
 #pragma unroll

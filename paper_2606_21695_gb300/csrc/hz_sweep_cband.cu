@@ -1,0 +1,357 @@
+// Cluster of warp bands: FP32 DD sweep (Algorithm 1) for subdomains wider
+// than 32 node columns, degree dividing 32 (P = 1, 2, 4), fixed WaveHoltz
+// count.
+//
+// A subdomain of nlx x NY nodes is cut into column bands of 32 nodes, one CTA
+// of a thread-block cluster each (CN = ceil(nlx / 32) CTAs); inside a CTA the
+// NY rows are cut into W row bands of at most 17 rows, one warp each.  Lane l
+// of a warp owns node column 32 q + l of its CTA q and the warp's rows of it
+// in registers for the whole WaveHoltz loop, as in the one-warp kernel
+// (hz_sweep_warp.cuh): y taps from registers with compile-time coefficients,
+// x part by the element gather and hand-off inside the band
+// (hz_sweep_xrow.cuh, XRowBand).  Per time step a warp publishes
+//   - its first and last P rows to a shared exchange buffer (the warps above
+//     and below read them as y halo), and
+//   - the band's edge columns to the neighbouring CTAs through distributed
+//     shared memory: lanes 32-P .. 31 into the right neighbour's left halo,
+//     lane 0 into the left neighbour's right halo,
+// then one cluster barrier (release / acquire) makes all of it visible; the
+// buffers are double-buffered by step parity, so one barrier per step is
+// enough (a buffer is rewritten two steps later, after every thread passed
+// the barrier that follows its last read).
+//
+// Arithmetic as in the other sweeps: modified leapfrog, eq. (WaveHoltz) with
+// the -1/(i omega) sign and 2/N_t scaling, lambda update -lambda - 2ik u;
+// beta' = beta Wx Wy with the lumped weights folded into the stencil.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "hz_gll_const.h"
+#include "hz_internal.h"
+#include "hz_sweep_warp.cuh"
+#include "hz_sweep_xrow.cuh"
+
+namespace hz {
+namespace cband {
+namespace {
+
+namespace cg = cooperative_groups;
+
+template <int P, int SY>
+struct Shape {
+  static constexpr int NY = SY * P + 1;
+  static constexpr int W = (NY + 16) / 17;      // row bands (warps per CTA)
+  static constexpr int RB = (NY + W - 1) / W;   // rows per band (the last may be shorter)
+  static_assert(NY - (W - 1) * RB >= P, "every row band must hold at least P rows");
+  static_assert(32 % P == 0, "bands must start on element boundaries");
+  static_assert(W >= 2, "rows 0 and NY-1 must lie in different bands");
+};
+
+template <int P, int SY>
+struct Smem {
+  using S = Shape<P, SY>;
+  float xb[2][S::W][2][P][32];  // row halos: [parity][band][first / last P rows][k][lane]
+  float hl[2][S::NY][P];        // left column halo: columns c0-P .. c0-1
+  float hr[2][S::NY];           // right column halo: column c0+32
+  float4 ecol[S::NY];           // this CTA's edge column (W or E): alpha-1, beta b
+};
+
+template <int P, int SY, bool SRC, int B>
+__device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int CN, int lane, Smem<P, SY>& sm,
+                                          Smem<P, SY>* right, Smem<P, SY>* left, cg::cluster_group& cluster) {
+  using S = Shape<P, SY>;
+  constexpr int NY = S::NY;
+  constexpr int J0 = B * S::RB;
+  constexpr int J1 = (B + 1) * S::RB < NY ? (B + 1) * S::RB : NY;
+  constexpr int NR = J1 - J0;
+  constexpr bool HAS_LO = B > 0, HAS_HI = B < S::W - 1;
+  const int sxi = l % a.Sx, syi = l / a.Sx;
+  const int nlx = a.nlx;
+  const int c0 = 32 * q;
+  const int c = c0 + lane;
+  const bool live = c < nlx;
+
+  // ---- x row (band form) and weights
+  auto wx = [&](int cc) {
+    const int ac = cc % P, ec_ = cc / P;
+    return a.hx2 * ((ec_ < a.sxe ? a.w[ac] : 0.0) + (ac == 0 && ec_ >= 1 ? a.w[P] : 0.0));
+  };
+  const double wx_lane = live ? wx(c) : 0.0;
+  XRowBand<P> xr;
+  xr.init(lane, c0, nlx, a.sxe, a.Kref, a.kxs, wx);
+
+  // ---- node data of the band's rows
+  const int64_t nn = (int64_t)nlx * NY;
+  const float* betaG = static_cast<const float*>(a.beta) + (int64_t)l * nn;
+  const float* alphaG = static_cast<const float*>(a.alpha) + (int64_t)l * nn;
+  const double* lamL = a.lam_in + (int64_t)l * 4 * a.NE * 2;
+  const bool ifW = sxi > 0, ifE = sxi < a.Sx - 1, ifS = syi > 0, ifN = syi < a.Sy - 1;
+  const bool edge = live && (c == 0 || c == nlx - 1);
+  constexpr int NB = SRC ? NR : 1;
+  float bet[NR];
+  float bbr[NB], bbi[NB];
+  float alE = 1.f, bEr = 0.f, bEi = 0.f;  // row 0 (band 0) or row NY-1 (last band)
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const int j = J0 + r;
+    double be = 0.0, al = 1.0, br = 0.0, bi = 0.0;
+    if (live) {
+      const int64_t n = (int64_t)j * nlx + c;
+      be = (double)betaG[n];
+      al = (double)alphaG[n];
+      if (SRC) {
+        const double shx = ((c == 0 && ifW) || (c == nlx - 1 && ifE)) ? 0.5 : 1.0;
+        const double shy = ((j == 0 && ifS) || (j == NY - 1 && ifN)) ? 0.5 : 1.0;
+        const int64_t I = (int64_t)sxi * a.snxP + c, J = (int64_t)syi * a.snyP + j;
+        const double* src = a.rhs + 2 * (J * a.NXg + I);
+        br = shx * shy * src[0];
+        bi = shx * shy * src[1];
+      }
+      if (c == 0 && ifW) { br += a.wys[j] * lamL[2 * (0 * a.NE + j)]; bi += a.wys[j] * lamL[2 * (0 * a.NE + j) + 1]; }
+      if (c == nlx - 1 && ifE) { br += a.wys[j] * lamL[2 * (1 * a.NE + j)]; bi += a.wys[j] * lamL[2 * (1 * a.NE + j) + 1]; }
+      if (j == 0 && ifS) { br += a.wxs[c] * lamL[2 * (2 * a.NE + c)]; bi += a.wxs[c] * lamL[2 * (2 * a.NE + c) + 1]; }
+      if (j == NY - 1 && ifN) { br += a.wxs[c] * lamL[2 * (3 * a.NE + c)]; bi += a.wxs[c] * lamL[2 * (3 * a.NE + c) + 1]; }
+    }
+    const int ay = j % P, ey = j / P;
+    const double wy = a.hy2 * ((ey < a.sye ? a.w[ay] : 0.0) + (ay == 0 && ey >= 1 ? a.w[P] : 0.0));
+    bet[r] = (float)(be * wx_lane * wy);  // beta' = beta Wx Wy
+    const float fbr = (float)(be * br), fbi = (float)(be * bi);
+    if (SRC) {
+      bbr[r] = fbr;
+      bbi[r] = fbi;
+    }
+    if (j == 0 || j == NY - 1) {
+      alE = (float)al;
+      bEr = SRC ? 0.f : fbr;
+      bEi = SRC ? 0.f : fbi;
+    } else if (edge) {
+      sm.ecol[j] = make_float4((float)(al - 1.0), SRC ? 0.f : fbr, SRC ? 0.f : fbi, 0.f);
+    }
+  }
+  __syncwarp();
+
+  const float4* tab = static_cast<const float4*>(a.tab);
+  const float sigma = (float)a.sigma, omega = (float)a.omega;
+  const float cpi = (float)a.cpi, spi = (float)a.spi, scale = (float)a.two_over_nt;
+  const float sy = (float)(4.0 / ((2.0 * a.hy2) * (2.0 * a.hy2)));  // 4 / hy^2
+  const int Nt = a.Nt, m_wh = a.m_wh;
+  const bool push_right = q < CN - 1 && lane >= 32 - P;
+  const bool push_left = q > 0 && lane == 0;
+  float p[NR], pd[NR], vre[NR], vim[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) { vre[r] = 0.f; vim[r] = 0.f; }
+
+  // buffer parity runs on across WaveHoltz iterations: consecutive time steps
+  // always alternate buffers (N_t - 1 may be odd), which the single barrier
+  // per step relies on
+  int cur = 0;
+  for (int m = 0; m < m_wh; ++m) {
+    {
+      const float4 t0 = tab[0];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        p[r] = vre[r];
+        pd[r] = omega * (vim[r] * cpi - vre[r] * spi);  // Re{-i w u e^{-i pi/N_t}}
+        vre[r] = t0.z * p[r];
+        vim[r] = t0.w * pd[r];
+      }
+    }
+    float4 tb = tab[1];
+    for (int nu = 1; nu < Nt; ++nu) {
+      const float4 tn = tab[nu + 1];  // prefetch (the table has N_t + 1 entries)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) p[r] += sigma * pd[r];
+      if (HAS_LO) {
+#pragma unroll
+        for (int k = 0; k < P; ++k) sm.xb[cur][B][0][k][lane] = p[k];
+      }
+      if (HAS_HI) {
+#pragma unroll
+        for (int k = 0; k < P; ++k) sm.xb[cur][B][1][k][lane] = p[NR - P + k];
+      }
+      if (push_right) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) right->hl[cur][J0 + r][lane - (32 - P)] = p[r];
+      }
+      if (push_left) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) left->hr[cur][J0 + r] = p[r];
+      }
+      cluster.sync();
+      float lo[P], hi[P];
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        lo[k] = HAS_LO ? sm.xb[cur][B - 1 >= 0 ? B - 1 : 0][1][k][lane] : 0.f;  // rows J0-P+k
+        hi[k] = HAS_HI ? sm.xb[cur][B + 1 < S::W ? B + 1 : 0][0][k][lane] : 0.f;  // rows J1+k
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const int j = J0 + r;
+        // (A p)_j / (Wx Wy): y taps (registers and halo rows, compile-time
+        // coefficients times 4/hy^2), x part in the band plus the column halos
+        float Y = 0.f;
+#pragma unroll
+        for (int t = -P; t <= P; ++t) {
+          const int jj = j + t;
+          if (warp_sweep::tap(P, SY, j, t) && jj >= 0 && jj < NY) {
+            const float v = (jj < J0) ? lo[jj - (J0 - P)] : (jj >= J1) ? hi[jj - J1] : p[jj - J0];
+            Y += kYRows.c[P - 1][gllc::row_class(P, SY, j)][t + P] * v;
+          }
+        }
+        float hL[P];
+#pragma unroll
+        for (int b = 0; b < P; ++b) hL[b] = sm.hl[cur][j][b];
+        const float Ap = xr.apply(p[r], lane, sm.hr[cur][j], hL) + sy * Y;
+        float f = pd[r] - bet[r] * Ap;
+        if (j == 0 || j == NY - 1) {
+          f += (alE - 1.f) * pd[r] + bEr * tb.x + bEi * tb.y;
+        } else {
+          f = edge_fix(f, pd[r], &sm.ecol[j], edge, tb.x, tb.y);
+        }
+        if (SRC) f += bbr[r] * tb.x + bbi[r] * tb.y;
+        pd[r] = f;
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        vre[r] += tb.z * p[r];
+        vim[r] += tb.w * pd[r];
+      }
+      tb = tn;
+      cur ^= 1;
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      vre[r] *= scale;  // u^{(m+1)} = (2/N_t) v
+      vim[r] *= scale;
+    }
+  }
+
+  // ---- outputs
+  bool bad = false;
+  if (live) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (!isfinite(vre[r]) || !isfinite(vim[r])) bad = true;
+      if (a.u_sub) {
+        const int64_t n = (int64_t)l * nn + (int64_t)(J0 + r) * nlx + c;
+        a.u_sub[2 * n] = (double)vre[r];
+        a.u_sub[2 * n + 1] = (double)vim[r];
+      }
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.flags, 1);
+  if (q == 0 && B == 0 && lane == 0 && a.wh_iter_max) {
+    atomicMax(a.wh_iter_max, m_wh);
+    atomicAdd(a.wh_iter_sum, (unsigned long long)m_wh);
+  }
+  const int NE = a.NE;
+  const double* kedgeL = a.kedge + (int64_t)l * 4 * NE;
+  auto put = [&](int e, int t, bool has, double ur, double ui) {
+    const bool iface = (e == 0) ? ifW : (e == 1) ? ifE : (e == 2) ? ifS : ifN;
+    const int len = (e < 2) ? NY : nlx;
+    double* dst;
+    if (iface) {
+      const int r = (e == 0) ? l - 1 : (e == 1) ? l + 1 : (e == 2) ? l - a.Sx : l + a.Sx;
+      dst = a.lam_out + 2 * (((int64_t)r * 4 + (e ^ 1)) * NE + t);
+    } else {
+      dst = a.lam_out + 2 * (((int64_t)l * 4 + e) * NE + t);
+    }
+    if (iface && t < len && has) {
+      const double kk = kedgeL[e * NE + t];
+      const double lr = lamL[2 * (e * NE + t)], li = lamL[2 * (e * NE + t) + 1];
+      dst[0] = -lr + 2.0 * kk * ui;
+      dst[1] = -li - 2.0 * kk * ur;
+    } else {
+      dst[0] = 0.0;
+      dst[1] = 0.0;
+    }
+  };
+  if (B == 0 && live) put(2, c, true, (double)vre[0], (double)vim[0]);                  // S edge: row 0
+  if (B == S::W - 1 && live) put(3, c, true, (double)vre[NR - 1], (double)vim[NR - 1]);  // N edge: row NY-1
+  if (edge) {  // W / E edges: this band's rows
+#pragma unroll
+    for (int r = 0; r < NR; ++r) put(c == 0 ? 0 : 1, J0 + r, true, (double)vre[r], (double)vim[r]);
+  }
+  if (q == 0) {  // padding entries of the edge slots (NE = max(nlx, NY))
+    if (B == 0)
+      for (int t = nlx + lane; t < NE; t += 32) put(2, t, false, 0.0, 0.0);
+    if (B == S::W - 1)
+      for (int t = nlx + lane; t < NE; t += 32) put(3, t, false, 0.0, 0.0);
+    if (B == 0 && lane == 0)
+      for (int t = NY; t < NE; ++t) {
+        put(0, t, false, 0.0, 0.0);
+        put(1, t, false, 0.0, 0.0);
+      }
+  }
+}
+
+template <int P, int SY, bool SRC>
+__global__ void __launch_bounds__(Shape<P, SY>::W * 32) sweep_cband_kernel(const __grid_constant__ SweepArgs a) {
+  using S = Shape<P, SY>;
+  __shared__ Smem<P, SY> sm;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int q = (int)cluster.block_rank();
+  const int CN = (int)cluster.num_blocks();
+  const int l = blockIdx.x / CN;  // the whole cluster shares one subdomain
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // zero the halos (read before any neighbour writes at the domain edges)
+  {
+    float* z = reinterpret_cast<float*>(&sm);
+    for (int k = threadIdx.x; k < (int)(sizeof(sm) / sizeof(float)); k += blockDim.x) z[k] = 0.f;
+  }
+  Smem<P, SY>* right = q < CN - 1 ? cluster.map_shared_rank(&sm, q + 1) : nullptr;
+  Smem<P, SY>* left = q > 0 ? cluster.map_shared_rank(&sm, q - 1) : nullptr;
+  cluster.sync();  // every CTA's buffers zeroed before any neighbour pushes into them
+#define HZ_BAND(BB)                                                                                    \
+  if (BB < S::W) {                                                                                     \
+    if (w == BB) band_body<P, SY, SRC, (BB < S::W ? BB : 0)>(a, l, q, CN, lane, sm, right, left, cluster); \
+  }
+  HZ_BAND(0) HZ_BAND(1) HZ_BAND(2) HZ_BAND(3) HZ_BAND(4) HZ_BAND(5) HZ_BAND(6) HZ_BAND(7)
+#undef HZ_BAND
+  cluster.sync();  // no CTA leaves while a neighbour may still touch its shared memory
+}
+
+template <int P, int SY>
+hz_status launch(const SweepArgs& a, int L, cudaStream_t st) {
+  using S = Shape<P, SY>;
+  static_assert(S::W <= 8, "at most 8 row bands");
+  const int CN = (a.nlx + 31) / 32;
+  if (CN < 2 || CN > 8) return HZ_ERR_UNSUPPORTED;
+  auto kern = a.rhs ? sweep_cband_kernel<P, SY, true> : sweep_cband_kernel<P, SY, false>;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(L * CN));
+  cfg.blockDim = dim3((unsigned)(S::W * 32));
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)CN;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess || clusters < 1) {
+    (void)cudaGetLastError();
+    return HZ_ERR_UNSUPPORTED;
+  }
+  HZ_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
+  note_launch();
+  return HZ_OK;
+}
+
+}  // namespace
+}  // namespace cband
+
+hz_status launch_sweep_cband(int P, const SweepArgs& a, int L, cudaStream_t st) {
+  if (a.wh_tol > 0.0 || a.round_mode != 0) return HZ_ERR_UNSUPPORTED;  // fixed WaveHoltz count, FP32 only
+  if (a.nlx <= 32) return HZ_ERR_UNSUPPORTED;
+  const int sy = (a.nly - 1) / P;
+  if (P == 4 && sy == 32) return cband::launch<4, 32>(a, L, st);
+  if (P == 4 && sy == 16) return cband::launch<4, 16>(a, L, st);
+  if (P == 2 && sy == 32) return cband::launch<2, 32>(a, L, st);
+  if (P == 2 && sy == 16) return cband::launch<2, 16>(a, L, st);
+  return HZ_ERR_UNSUPPORTED;
+}
+
+}  // namespace hz

@@ -167,6 +167,10 @@ __global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_k
   __shared__ double part[2];
   __shared__ int stop_flag;
   int m_done = 0;
+  // buffer parity runs on across WaveHoltz iterations: consecutive time steps
+  // always alternate buffers (N_t - 1 may be odd), which the single barrier
+  // per step relies on
+  int cur = 0;
   for (int m = 0; m < a.m_wh; ++m) {
     const bool check = a.wh_tol > 0.0;
     if (check && active) {
@@ -184,7 +188,6 @@ __global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_k
         vim[r] = t0.w * pd[r];
       }
     }
-    int cur = 0;
     for (int nu = 1; nu < a.Nt; ++nu) {
       const float4 tb = tab[nu];
       float* bufc = cur ? buf1 : buf0;

@@ -176,6 +176,10 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(const __grid_constant__ Swe
   __shared__ double red[2 * 32];
   __shared__ int stop_flag;
   int m_done = 0;
+  // buffer parity runs on across WaveHoltz iterations: consecutive time steps
+  // always alternate buffers (N_t - 1 may be odd), which the single barrier
+  // per step relies on
+  int cur = 0;
   for (int m = 0; m < a.m_wh; ++m) {
     Real p[RY], pd[RY], vre[RY], vim[RY];
     {
@@ -188,7 +192,6 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(const __grid_constant__ Swe
         vim[r] = t0.w * pd[r];
       }
     }
-    int cur = 0;
     for (int nu = 1; nu < a.Nt; ++nu) {
       const Tab tb = tab[nu];
       Real* bufc = cur ? buf1 : buf0;

@@ -65,6 +65,68 @@ struct XRow {
   }
 };
 
+// The same x part for a band of 32 node columns c0 .. c0+31 of a wider
+// subdomain (one warp of a cluster; the degree divides 32, so bands start on
+// element boundaries).  Inside the band it is XRow's gather and hand-off;
+// across the band's ends two halo inputs complete it: the node just past the
+// band (needed by the band's last element: coefficient kR) and the P nodes
+// before it (the element to the left of the band's first column: kL).
+template <int P>
+struct XRowBand {
+  int src[P + 1];
+  float kown[P + 1];
+  float kl[P + 1];
+  float kR;     // coefficient of column c0+32 (0 if this lane's element ends inside the band)
+  float kL[P];  // coefficients of columns c0-P .. c0-1 (lane 0 of a band with c0 > 0 only)
+
+  template <typename WX>
+  __device__ __forceinline__ void init(int lane, int c0, int nlx, int sxe, const double* Kref, double kxs, WX wx) {
+    const int c = c0 + lane;
+    const int a = c % P, e = c / P;
+    const bool live = c < nlx;
+    const bool own = live && e < sxe;
+    const bool left = live && a == 0 && e >= 1;
+    const double s_me = live ? kxs / wx(c) : 0.0;
+    // hand-off inside the band only (lane 31's part would belong to the next band)
+    const bool sends = live && (a == P - 1) && (c + 1 < nlx) && (lane + 1 < 32);
+    const double s_nb = sends ? kxs / wx(c + 1) : 0.0;
+    kR = 0.f;
+    for (int k = 0; k <= P; ++k) {
+      const int b = (a + k) % (P + 1);
+      const int sl = e * P + b - c0;  // lane of that node in this band (32: past its end)
+      src[k] = sl & 31;
+      double v = 0.0;
+      if (own) v += Kref[a * (P + 1) + b];
+      if (k == 0 && left) v += Kref[P * (P + 1) + P];
+      float kv = (float)(v * s_me);
+      if (k > 0 && sl >= 32) {
+        kR = kv;
+        kv = 0.f;
+      }
+      kown[k] = kv;
+      kl[k] = (sends && k != 1) ? (float)(Kref[P * (P + 1) + b] * s_nb) : 0.f;
+    }
+    const bool lh = left && lane == 0;  // the element to the left lies in the previous band
+    for (int b = 0; b < P; ++b) kL[b] = lh ? (float)(Kref[P * (P + 1) + b] * s_me) : 0.f;
+  }
+
+  // hR: p at column c0+32; hL[b]: p at column c0-P+b.
+  __device__ __forceinline__ float apply(float pj, int lane, float hR, const float (&hL)[P]) const {
+    float own = kown[0] * pj;
+    float lp = kl[0] * pj;
+#pragma unroll
+    for (int k = 1; k <= P; ++k) {
+      const float v = __shfl_sync(0xffffffffu, pj, src[k]);
+      own += kown[k] * v;
+      if (k != 1) lp += kl[k] * v;
+    }
+    own += kR * hR;
+#pragma unroll
+    for (int b = 0; b < P; ++b) own += kL[b] * hL[b];
+    return own + __shfl_sync(0xffffffffu, lp, (lane + 31) & 31);  // lane 31 sends nothing
+  }
+};
+
 // Edge-column correction of the p-dot update of a row.  The interior update
 // is f = p-dot - beta' A p; the two edge lanes add (alpha - 1) p-dot +
 // beta b_re cos + beta b_im sin with (alpha - 1, beta b_re, beta b_im) read

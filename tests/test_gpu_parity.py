@@ -390,10 +390,37 @@ def test_sweep_fp32_cluster_matches_oracle(hz, monkeypatch, nx, ny, sx, sy, P, t
     assert _rel(u1, ref4) < 1e-3
 
 
-def test_config3_full_size_sampled_sweep(hz):
+CBAND_LAYOUTS = [
+    (32, 16, 16, 16, 4),  # 65 x 65 nodes: 3 column bands (the last one column wide), 4 row bands
+    (16, 32, 16, 32, 2),  # 33 x 65 nodes, single subdomain, P = 2
+    (32, 32, 16, 16, 2),  # 2 x 2 subdomains of 33 x 33 nodes: 2 row bands
+    (24, 16, 8, 16, 4),   # 33 x 65 nodes, 3 x 1 subdomains (interfaces in x)
+]
+
+
+@pytest.mark.parametrize("nx,ny,sx,sy,P", CBAND_LAYOUTS)
+def test_sweep_fp32_cluster_bands_match_oracle(hz, monkeypatch, nx, ny, sx, sy, P):
+    """Subdomains wider than 32 node columns on a cluster of 32-column bands
+    (register-resident rows per warp, halos through distributed shared
+    memory), with and without the source, against the oracle."""
+    monkeypatch.setenv("HZ_SWEEP_VARIANT", "cband")
+    wl = _wl(nx, ny, sx, sy, P)
+    case, pr = _pair(hz, wl, g_seed=nx + 3 * P)
+    nt = hz.hz_problem_nt(case.pr)
+    lam = _rand_lam(pr, 8)
+    for with_rhs in (True, False):
+        got_l, got_u = _run_sweep(hz, case, pr, hz.HZ_FP32_REFINE, nt, 3, lam, with_rhs)
+        ref_l, ref_u, _ = pr.sweep(lam, pr.rhs() if with_rhs else None, nt, 3, want_u=True)
+        assert np.all(np.isfinite(got_l))
+        assert _rel(got_u, ref_u) < 2e-4 and _rel(got_l, ref_l) < 2e-4
+
+
+@pytest.mark.parametrize("variant", ["cband", "cluster"])
+def test_config3_full_size_sampled_sweep(hz, monkeypatch, variant):
     """1024x1024 quads, P = 4, 32x32 subdomains of 32x32 elements (16641
-    nodes each): the cluster kernel at full size, sampled subdomains
+    nodes each): both cluster kernels at full size, sampled subdomains
     recomputed by the oracle."""
+    monkeypatch.setenv("HZ_SWEEP_VARIANT", variant)
     wl = configs.config3()
     case, pr = _pair(hz, wl)
     nt = hz.hz_problem_nt(case.pr)
