@@ -61,7 +61,9 @@ def parse():
     ap.add_argument("--baseline-requests", type=int, default=12)
     ap.add_argument("--sweeps", type=int, default=2)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
-    ap.add_argument("--wh-iters", type=int, default=20)
+    ap.add_argument("--wh-iters", type=int, default=20, help="WaveHoltz iterations per sweep")
+    ap.add_argument("--max-sweeps", type=int, default=5000)
+    ap.add_argument("--max-refine", type=int, default=20)
     ap.add_argument("--workload", choices=["cfg1", "cfg2", "cfg3", "cfg3s"], default="cfg2",
                     help="cfg2 is the benchmark workload; cfg1/cfg3 are reported separately; cfg3s is the "
                          "cfg3 physics and subdomain shape on a 256x256 mesh (for profiling)")
@@ -212,8 +214,8 @@ def run_ours(args):
     case = Case(wl, device=local)
     n = case.n
     stream = torch.cuda.current_stream()
-    opts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, inner_tol=1e-2, wh_iters=20,
-                              gmres_restart=60, max_sweeps=5000)
+    opts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, inner_tol=1e-2, wh_iters=args.wh_iters,
+                              gmres_restart=60, max_sweeps=args.max_sweeps, max_refine=args.max_refine)
     u = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
@@ -287,8 +289,8 @@ def run_ours(args):
         # plain-FP64 time to the same tolerance, one solve (outside the timed region)
         fp64 = None
         if not args.no_fp64:
-            o64 = hz.hz_default_opts(precision=hz.HZ_FP64, tol=TOL, inner_tol=1e-2, wh_iters=20, gmres_restart=60,
-                                     max_sweeps=5000)
+            o64 = hz.hz_default_opts(precision=hz.HZ_FP64, tol=TOL, inner_tol=1e-2, wh_iters=args.wh_iters,
+                                     gmres_restart=60, max_sweeps=args.max_sweeps, max_refine=args.max_refine)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)

@@ -253,7 +253,9 @@ hz_status launch_choice(Problem& pr, const SweepArgs& a0, Choice c, bool fp32, c
     s = launch_sweep_warp(g.P, g.sny, c.ty > 0 ? c.ty : 1, w, st);
   } else if (c.variant == kVariantClusterBand) {
     if (!fp32) return HZ_ERR_UNSUPPORTED;
-    s = launch_sweep_cband(g.P, a0, g.L, st);
+    SweepArgs a = a0;
+    a.ty_force = c.ty;  // 8: 8 rows per warp band, else 16
+    s = launch_sweep_cband(g.P, a, g.L, st);
   } else if (c.variant == kVariantCluster) {
     if (!fp32) return HZ_ERR_UNSUPPORTED;
     SweepArgs a = a0;
@@ -343,7 +345,7 @@ hz_status autotune(Problem& pr, int precision, int nt, int m_wh, cudaStream_t st
   std::vector<Choice> cands;
   if (fp32)
     cands = {{kVariantWarp, 1}, {kVariantWarp, 2}, {kVariantWarp, 4}, {kVariantBlock, 1}, {kVariantBlock, 2},
-             {kVariantCluster, 0}, {kVariantCluster, 4}, {kVariantClusterBand, 0}};
+             {kVariantCluster, 0}, {kVariantCluster, 4}, {kVariantClusterBand, 0}, {kVariantClusterBand, 8}};
   else cands = {{kVariantBlock, 1}, {kVariantBlock, 2}};
   cudaEvent_t e0, e1;
   HZ_CUDA(cudaEventCreate(&e0));
@@ -448,7 +450,9 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
   }
   const bool small_block = (int64_t)g.nlx * ((g.nly + g.P - 1) / g.P) <= 256;
   if (ls == HZ_ERR_UNSUPPORTED && fp32 && want == kVariantClusterBand) {  // else only when autotuned
-    ls = launch_choice(pr, a, Choice{kVariantClusterBand, 0}, fp32, st);
+    // HZ_CBAND_ROWS=8 forces 8-row warp bands (tests)
+    const char* cr = std::getenv("HZ_CBAND_ROWS");
+    ls = launch_choice(pr, a, Choice{kVariantClusterBand, cr ? std::atoi(cr) : 0}, fp32, st);
     if (ls != HZ_OK && ls != HZ_ERR_UNSUPPORTED) return ls;
     if (ls != HZ_OK && want == kVariantClusterBand)
       return fail(HZ_ERR_UNSUPPORTED, "no cluster-of-bands sweep shape fits");

@@ -4,14 +4,21 @@
 //
 // A subdomain of nlx x NY nodes is cut into column bands of 32 nodes, one CTA
 // of a thread-block cluster each (CN = ceil(nlx / 32) CTAs); inside a CTA the
-// NY rows are cut into W row bands of at most 17 rows, one warp each.  Lane l
-// of a warp owns node column 32 q + l of its CTA q and the warp's rows of it
-// in registers for the whole WaveHoltz loop, as in the one-warp kernel
-// (hz_sweep_warp.cuh): y taps from registers with compile-time coefficients,
-// x part by the element gather and hand-off inside the band
-// (hz_sweep_xrow.cuh, XRowBand).  Per time step a warp publishes
-//   - its first and last P rows to a shared exchange buffer (the warps above
-//     and below read them as y halo), and
+// NY = 16 W + 1 rows are cut into W row bands, one warp each: band B holds
+// rows 16 B .. 16 B + 16 (17 rows; the last is also the next band's first,
+// computed by both warps with identical arithmetic, so the copies agree
+// bitwise).  Every warp runs the same code with B a run-time value -- one
+// instruction stream per SM instead of one per band (separate fully unrolled
+// bodies per band overflow the instruction cache).  Lane l of a warp owns
+// node column 32 q + l of its CTA q and the warp's rows of it in registers
+// for the whole WaveHoltz loop, as in the one-warp kernel (hz_sweep_warp.cuh):
+// y taps from registers with compile-time coefficients (element-boundary
+// rows use the two-element row; the subdomain's first and last rows are
+// corrected to their one-element rows), x part by the element gather and
+// hand-off inside the band (hz_sweep_xrow.cuh, XRowBand).  Per time step a
+// warp publishes
+//   - its rows 1..P and 16-P..15 to a shared exchange buffer (the warps
+//     below and above read them as y halo), and
 //   - the band's edge columns to the neighbouring CTAs through distributed
 //     shared memory: lanes 32-P .. 31 into the right neighbour's left halo,
 //     lane 0 into the left neighbour's right halo,
@@ -37,34 +44,37 @@ namespace {
 
 namespace cg = cooperative_groups;
 
-template <int P, int SY>
+// RB rows per band (16, or 8 for twice the warps at half the registers)
+template <int P, int SY, int RB_>
 struct Shape {
   static constexpr int NY = SY * P + 1;
-  static constexpr int W = (NY + 16) / 17;      // row bands (warps per CTA)
-  static constexpr int RB = (NY + W - 1) / W;   // rows per band (the last may be shorter)
-  static_assert(NY - (W - 1) * RB >= P, "every row band must hold at least P rows");
-  static_assert(32 % P == 0, "bands must start on element boundaries");
-  static_assert(W >= 2, "rows 0 and NY-1 must lie in different bands");
+  static constexpr int RB = RB_;                // rows per band (+1 shared with the next band)
+  static constexpr int NR = RB + 1;             // register rows per warp
+  static constexpr int W = (NY - 1) / RB;       // row bands (warps per CTA)
+  static_assert((NY - 1) % RB == 0 && RB % P == 0, "bands of RB rows on element boundaries");
+  static_assert(32 % P == 0, "column bands must start on element boundaries");
+  static_assert(W >= 2 && W <= 32, "2 to 32 row bands");
 };
 
-template <int P, int SY>
+template <int P, int SY, int RB>
 struct Smem {
-  using S = Shape<P, SY>;
+  using S = Shape<P, SY, RB>;
   float xb[2][S::W][2][P][32];  // row halos: [parity][band][first / last P rows][k][lane]
   float hl[2][S::NY][P];        // left column halo: columns c0-P .. c0-1
   float hr[2][S::NY];           // right column halo: column c0+32
   float4 ecol[S::NY];           // this CTA's edge column (W or E): alpha-1, beta b
 };
 
-template <int P, int SY, bool SRC, int B>
-__device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int CN, int lane, Smem<P, SY>& sm,
-                                          Smem<P, SY>* right, Smem<P, SY>* left, cg::cluster_group& cluster) {
-  using S = Shape<P, SY>;
+template <int P, int SY, int RB, bool SRC>
+__device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int CN, int B, int lane,
+                                          Smem<P, SY, RB>& sm, Smem<P, SY, RB>* right, Smem<P, SY, RB>* left,
+                                          cg::cluster_group& cluster) {
+  using S = Shape<P, SY, RB>;
   constexpr int NY = S::NY;
-  constexpr int J0 = B * S::RB;
-  constexpr int J1 = (B + 1) * S::RB < NY ? (B + 1) * S::RB : NY;
-  constexpr int NR = J1 - J0;
-  constexpr bool HAS_LO = B > 0, HAS_HI = B < S::W - 1;
+  constexpr int NR = S::NR;
+  constexpr int W = S::W;
+  const int J0 = S::RB * B;
+  const bool first = B == 0, last = B == W - 1;  // the band holds row 0 / row NY-1
   const int sxi = l % a.Sx, syi = l / a.Sx;
   const int nlx = a.nlx;
   const int c0 = 32 * q;
@@ -90,7 +100,7 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
   constexpr int NB = SRC ? NR : 1;
   float bet[NR];
   float bbr[NB], bbi[NB];
-  float alE = 1.f, bEr = 0.f, bEi = 0.f;  // row 0 (band 0) or row NY-1 (last band)
+  float alE = 1.f, bEr = 0.f, bEi = 0.f;  // row 0 (first band) or row NY-1 (last band)
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
     const int j = J0 + r;
@@ -134,6 +144,11 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
   const float sigma = (float)a.sigma, omega = (float)a.omega;
   const float cpi = (float)a.cpi, spi = (float)a.spi, scale = (float)a.two_over_nt;
   const float sy = (float)(4.0 / ((2.0 * a.hy2) * (2.0 * a.hy2)));  // 4 / hy^2
+  // first / last subdomain row: the one-element row is 2 x the two-element row
+  // (w_0 = w_P; the missing side's halo is zero) minus the missing element's
+  // diagonal term: Kref[P][P] / w_0 for the first row, Kref[0][0] / w_P for the last
+  const float kc_first = kYRows.c[P - 1][P + 1][P];  // last-row class, t = 0: Kref[P][P] / w_P
+  const float kc_last = kYRows.c[P - 1][0][P];       // first-row class, t = 0: Kref[0][0] / w_0
   const int Nt = a.Nt, m_wh = a.m_wh;
   const bool push_right = q < CN - 1 && lane >= 32 - P;
   const bool push_left = q > 0 && lane == 0;
@@ -141,9 +156,7 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
 #pragma unroll
   for (int r = 0; r < NR; ++r) { vre[r] = 0.f; vim[r] = 0.f; }
 
-  // buffer parity runs on across WaveHoltz iterations: consecutive time steps
-  // always alternate buffers (N_t - 1 may be odd), which the single barrier
-  // per step relies on
+  // buffer parity runs on across WaveHoltz iterations (see the block kernel)
   int cur = 0;
   for (int m = 0; m < m_wh; ++m) {
     {
@@ -161,13 +174,11 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
       const float4 tn = tab[nu + 1];  // prefetch (the table has N_t + 1 entries)
 #pragma unroll
       for (int r = 0; r < NR; ++r) p[r] += sigma * pd[r];
-      if (HAS_LO) {
+      // y halos for the neighbouring warps: rows 1..P (to the band below), 16-P..15 (above)
 #pragma unroll
-        for (int k = 0; k < P; ++k) sm.xb[cur][B][0][k][lane] = p[k];
-      }
-      if (HAS_HI) {
-#pragma unroll
-        for (int k = 0; k < P; ++k) sm.xb[cur][B][1][k][lane] = p[NR - P + k];
+      for (int k = 0; k < P; ++k) {
+        sm.xb[cur][B][0][k][lane] = p[1 + k];
+        sm.xb[cur][B][1][k][lane] = p[S::RB - P + k];
       }
       if (push_right) {
 #pragma unroll
@@ -181,29 +192,40 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
       float lo[P], hi[P];
 #pragma unroll
       for (int k = 0; k < P; ++k) {
-        lo[k] = HAS_LO ? sm.xb[cur][B - 1 >= 0 ? B - 1 : 0][1][k][lane] : 0.f;  // rows J0-P+k
-        hi[k] = HAS_HI ? sm.xb[cur][B + 1 < S::W ? B + 1 : 0][0][k][lane] : 0.f;  // rows J1+k
+        lo[k] = first ? 0.f : sm.xb[cur][first ? 0 : B - 1][1][k][lane];  // rows J0-P+k
+        hi[k] = last ? 0.f : sm.xb[cur][last ? 0 : B + 1][0][k][lane];    // rows J0+17+k
       }
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         const int j = J0 + r;
-        // (A p)_j / (Wx Wy): y taps (registers and halo rows, compile-time
-        // coefficients times 4/hy^2), x part in the band plus the column halos
+        // (A p)_j / (Wx Wy): y taps of the row's class (compile-time: r % P,
+        // element-boundary rows with both elements), x part in the band plus
+        // the column halos
+        const int a_r = r % P;
+        const int cls = a_r == 0 ? P : a_r;
         float Y = 0.f;
 #pragma unroll
         for (int t = -P; t <= P; ++t) {
-          const int jj = j + t;
-          if (warp_sweep::tap(P, SY, j, t) && jj >= 0 && jj < NY) {
-            const float v = (jj < J0) ? lo[jj - (J0 - P)] : (jj >= J1) ? hi[jj - J1] : p[jj - J0];
-            Y += kYRows.c[P - 1][gllc::row_class(P, SY, j)][t + P] * v;
+          const bool tp = a_r == 0 ? true : (a_r + t >= 0 && a_r + t <= P);
+          if (tp) {
+            const int rr = r + t;
+            const float v = rr < 0 ? lo[rr + P] : rr >= NR ? hi[rr - NR] : p[rr];
+            Y += kYRows.c[P - 1][cls][t + P] * v;
           }
+        }
+        if (r == 0) {
+          if (first) Y = 2.f * Y - kc_first * p[r];
+        }
+        if (r == NR - 1) {
+          if (last) Y = 2.f * Y - kc_last * p[r];
         }
         float hL[P];
 #pragma unroll
         for (int b = 0; b < P; ++b) hL[b] = sm.hl[cur][j][b];
         const float Ap = xr.apply(p[r], lane, sm.hr[cur][j], hL) + sy * Y;
         float f = pd[r] - bet[r] * Ap;
-        if (j == 0 || j == NY - 1) {
+        const bool srow = (r == 0 && first) || (r == NR - 1 && last);
+        if (srow) {
           f += (alE - 1.f) * pd[r] + bEr * tb.x + bEi * tb.y;
         } else {
           f = edge_fix(f, pd[r], &sm.ecol[j], edge, tb.x, tb.y);
@@ -226,11 +248,13 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
     }
   }
 
-  // ---- outputs
+  // ---- outputs (row 16 of a band is the next band's row 0: written once, by that band)
+  const int nout = last ? NR : NR - 1;
   bool bad = false;
   if (live) {
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
+      if (r >= nout) break;
       if (!isfinite(vre[r]) || !isfinite(vim[r])) bad = true;
       if (a.u_sub) {
         const int64_t n = (int64_t)l * nn + (int64_t)(J0 + r) * nlx + c;
@@ -240,7 +264,7 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
     }
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.flags, 1);
-  if (q == 0 && B == 0 && lane == 0 && a.wh_iter_max) {
+  if (q == 0 && first && lane == 0 && a.wh_iter_max) {
     atomicMax(a.wh_iter_max, m_wh);
     atomicAdd(a.wh_iter_sum, (unsigned long long)m_wh);
   }
@@ -251,8 +275,8 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
     const int len = (e < 2) ? NY : nlx;
     double* dst;
     if (iface) {
-      const int r = (e == 0) ? l - 1 : (e == 1) ? l + 1 : (e == 2) ? l - a.Sx : l + a.Sx;
-      dst = a.lam_out + 2 * (((int64_t)r * 4 + (e ^ 1)) * NE + t);
+      const int rn = (e == 0) ? l - 1 : (e == 1) ? l + 1 : (e == 2) ? l - a.Sx : l + a.Sx;
+      dst = a.lam_out + 2 * (((int64_t)rn * 4 + (e ^ 1)) * NE + t);
     } else {
       dst = a.lam_out + 2 * (((int64_t)l * 4 + e) * NE + t);
     }
@@ -266,18 +290,19 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
       dst[1] = 0.0;
     }
   };
-  if (B == 0 && live) put(2, c, true, (double)vre[0], (double)vim[0]);                  // S edge: row 0
-  if (B == S::W - 1 && live) put(3, c, true, (double)vre[NR - 1], (double)vim[NR - 1]);  // N edge: row NY-1
+  if (first && live) put(2, c, true, (double)vre[0], (double)vim[0]);                  // S edge: row 0
+  if (last && live) put(3, c, true, (double)vre[NR - 1], (double)vim[NR - 1]);         // N edge: row NY-1
   if (edge) {  // W / E edges: this band's rows
 #pragma unroll
-    for (int r = 0; r < NR; ++r) put(c == 0 ? 0 : 1, J0 + r, true, (double)vre[r], (double)vim[r]);
+    for (int r = 0; r < NR; ++r)
+      if (r < nout) put(c == 0 ? 0 : 1, J0 + r, true, (double)vre[r], (double)vim[r]);
   }
   if (q == 0) {  // padding entries of the edge slots (NE = max(nlx, NY))
-    if (B == 0)
+    if (first)
       for (int t = nlx + lane; t < NE; t += 32) put(2, t, false, 0.0, 0.0);
-    if (B == S::W - 1)
+    if (last)
       for (int t = nlx + lane; t < NE; t += 32) put(3, t, false, 0.0, 0.0);
-    if (B == 0 && lane == 0)
+    if (first && lane == 0)
       for (int t = NY; t < NE; ++t) {
         put(0, t, false, 0.0, 0.0);
         put(1, t, false, 0.0, 0.0);
@@ -285,10 +310,9 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
   }
 }
 
-template <int P, int SY, bool SRC>
-__global__ void __launch_bounds__(Shape<P, SY>::W * 32) sweep_cband_kernel(const __grid_constant__ SweepArgs a) {
-  using S = Shape<P, SY>;
-  __shared__ Smem<P, SY> sm;
+template <int P, int SY, int RB, bool SRC>
+__global__ void __launch_bounds__(Shape<P, SY, RB>::W * 32) sweep_cband_kernel(const __grid_constant__ SweepArgs a) {
+  __shared__ Smem<P, SY, RB> sm;
   cg::cluster_group cluster = cg::this_cluster();
   const int q = (int)cluster.block_rank();
   const int CN = (int)cluster.num_blocks();
@@ -299,25 +323,19 @@ __global__ void __launch_bounds__(Shape<P, SY>::W * 32) sweep_cband_kernel(const
     float* z = reinterpret_cast<float*>(&sm);
     for (int k = threadIdx.x; k < (int)(sizeof(sm) / sizeof(float)); k += blockDim.x) z[k] = 0.f;
   }
-  Smem<P, SY>* right = q < CN - 1 ? cluster.map_shared_rank(&sm, q + 1) : nullptr;
-  Smem<P, SY>* left = q > 0 ? cluster.map_shared_rank(&sm, q - 1) : nullptr;
+  Smem<P, SY, RB>* right = q < CN - 1 ? cluster.map_shared_rank(&sm, q + 1) : nullptr;
+  Smem<P, SY, RB>* left = q > 0 ? cluster.map_shared_rank(&sm, q - 1) : nullptr;
   cluster.sync();  // every CTA's buffers zeroed before any neighbour pushes into them
-#define HZ_BAND(BB)                                                                                    \
-  if (BB < S::W) {                                                                                     \
-    if (w == BB) band_body<P, SY, SRC, (BB < S::W ? BB : 0)>(a, l, q, CN, lane, sm, right, left, cluster); \
-  }
-  HZ_BAND(0) HZ_BAND(1) HZ_BAND(2) HZ_BAND(3) HZ_BAND(4) HZ_BAND(5) HZ_BAND(6) HZ_BAND(7)
-#undef HZ_BAND
+  band_body<P, SY, RB, SRC>(a, l, q, CN, w, lane, sm, right, left, cluster);
   cluster.sync();  // no CTA leaves while a neighbour may still touch its shared memory
 }
 
-template <int P, int SY>
+template <int P, int SY, int RB>
 hz_status launch(const SweepArgs& a, int L, cudaStream_t st) {
-  using S = Shape<P, SY>;
-  static_assert(S::W <= 8, "at most 8 row bands");
+  using S = Shape<P, SY, RB>;
   const int CN = (a.nlx + 31) / 32;
   if (CN < 2 || CN > 8) return HZ_ERR_UNSUPPORTED;
-  auto kern = a.rhs ? sweep_cband_kernel<P, SY, true> : sweep_cband_kernel<P, SY, false>;
+  auto kern = a.rhs ? sweep_cband_kernel<P, SY, RB, true> : sweep_cband_kernel<P, SY, RB, false>;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(L * CN));
   cfg.blockDim = dim3((unsigned)(S::W * 32));
@@ -340,17 +358,24 @@ hz_status launch(const SweepArgs& a, int L, cudaStream_t st) {
   return HZ_OK;
 }
 
+template <int P, int SY>
+hz_status launch_rb(const SweepArgs& a, int L, cudaStream_t st) {
+  if (a.ty_force == 8) return launch<P, SY, 8>(a, L, st);
+  return launch<P, SY, 16>(a, L, st);
+}
+
 }  // namespace
 }  // namespace cband
 
 hz_status launch_sweep_cband(int P, const SweepArgs& a, int L, cudaStream_t st) {
   if (a.wh_tol > 0.0 || a.round_mode != 0) return HZ_ERR_UNSUPPORTED;  // fixed WaveHoltz count, FP32 only
   if (a.nlx <= 32) return HZ_ERR_UNSUPPORTED;
+  // rows per warp band: 16 (a.ty_force != 8) or 8
   const int sy = (a.nly - 1) / P;
-  if (P == 4 && sy == 32) return cband::launch<4, 32>(a, L, st);
-  if (P == 4 && sy == 16) return cband::launch<4, 16>(a, L, st);
-  if (P == 2 && sy == 32) return cband::launch<2, 32>(a, L, st);
-  if (P == 2 && sy == 16) return cband::launch<2, 16>(a, L, st);
+  if (P == 4 && sy == 32) return cband::launch_rb<4, 32>(a, L, st);
+  if (P == 4 && sy == 16) return cband::launch_rb<4, 16>(a, L, st);
+  if (P == 2 && sy == 32) return cband::launch_rb<2, 32>(a, L, st);
+  if (P == 2 && sy == 16) return cband::launch_rb<2, 16>(a, L, st);
   return HZ_ERR_UNSUPPORTED;
 }
 

@@ -398,12 +398,15 @@ CBAND_LAYOUTS = [
 ]
 
 
+@pytest.mark.parametrize("rows", ["16", "8"])
 @pytest.mark.parametrize("nx,ny,sx,sy,P", CBAND_LAYOUTS)
-def test_sweep_fp32_cluster_bands_match_oracle(hz, monkeypatch, nx, ny, sx, sy, P):
+def test_sweep_fp32_cluster_bands_match_oracle(hz, monkeypatch, nx, ny, sx, sy, P, rows):
     """Subdomains wider than 32 node columns on a cluster of 32-column bands
-    (register-resident rows per warp, halos through distributed shared
-    memory), with and without the source, against the oracle."""
+    (register-resident rows per warp, 16 or 8 rows per warp band, halos
+    through distributed shared memory), with and without the source, against
+    the oracle."""
     monkeypatch.setenv("HZ_SWEEP_VARIANT", "cband")
+    monkeypatch.setenv("HZ_CBAND_ROWS", rows)
     wl = _wl(nx, ny, sx, sy, P)
     case, pr = _pair(hz, wl, g_seed=nx + 3 * P)
     nt = hz.hz_problem_nt(case.pr)
