@@ -26,42 +26,37 @@ __device__ __forceinline__ void group_barrier(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// One subdomain (H warps) per block.  NY - 1 = SY P rows are cut into H bands
-// of RB = SY P / H rows (a multiple of P); band B holds rows B RB .. B RB + RB,
-// the last of which is also the next band's first row, computed by both warps
-// with the same arithmetic (the copies agree bitwise).  Every warp runs the
-// same code with B a run-time value, so the H warps share one instruction
-// stream (separate unrolled bodies per band compete for the instruction
-// cache).
+// One subdomain (H warps) per block.
 template <int P, int SY, int H>
 struct Shape {
   static constexpr int NY = SY * P + 1;
-  static constexpr int RB = (NY - 1) / H;  // rows per band (+1 shared with the next band)
-  static constexpr int NR = RB + 1;        // register rows per warp
-  static constexpr int G = 1;              // subdomains per block
-  static_assert((NY - 1) % H == 0 && RB % P == 0 && RB >= P, "bands of whole elements");
+  static constexpr int RB = (NY + H - 1) / H;  // rows per band (the last band may be shorter)
+  static constexpr int G = 1;                   // subdomains per block
 };
 
-template <int P, int SY, bool SRC, int H>
-__device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, int lane, int B, float* xbuf,
-                                          float4* ecg, float2* uo, double* red) {
+template <int P, int SY, bool SRC, int H, int B>
+__device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, int lane, float* xbuf, float4* ecg,
+                                          float2* uo, double* red) {
   using S = Shape<P, SY, H>;
   constexpr int NY = S::NY;
-  constexpr int NR = S::NR;
-  constexpr int RB = S::RB;
+  constexpr int J0 = B * S::RB;
+  constexpr int J1 = (B + 1) * S::RB < NY ? (B + 1) * S::RB : NY;
+  constexpr int NR = J1 - J0;
+  static_assert(NR >= P, "every band must hold at least P rows");
+  constexpr bool HAS_LO = B > 0, HAS_HI = B < H - 1;
   const SweepArgs& a = x.base;
-  const int J0 = B * RB;
-  const bool first = B == 0, last = B == H - 1;
   const int sxi = l % a.Sx, syi = l / a.Sx;
   const int nlx = a.nlx;
   const int i = lane;
   const bool live = i < nlx;
   const int bar_id = 1 + g;
 
-  // ---- x row (assembled, weights folded)
+  // ---- per-lane x row (scaled by 2/hx)
   const int ax = i % P, ex = i / P;
   const bool own_x = live && ex < a.sxe;
   const bool left_x = live && (ax == 0) && (ex >= 1);
+  // with beta' = beta Wx Wy the stiffness terms are divided by the lumped
+  // weights: (A p)/(Wx Wy) = (Kx p)/Wx + (Ky p)/Wy
   const double wx_lane = a.hx2 * ((own_x ? a.w[ax] : 0.0) + (left_x ? a.w[P] : 0.0));
   XRow<P> xr;
   xr.init(lane, nlx, a.sxe, a.Kref, a.kxs, [&](int c) {
@@ -79,11 +74,11 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
   constexpr int NB = SRC ? NR : 1;
   float bet[NR];
   float bbr[NB], bbi[NB];
-  float alE = 1.f, bEr = 0.f, bEi = 0.f;  // row 0 (first band) or row NY-1 (last band)
+  float alE = 0.f, bEr = 0.f, bEi = 0.f;  // row 0 (band 0) or row NY-1 (last band)
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
     const int j = J0 + r;
-    float be = 0.f, al = 1.f, br = 0.f, bi = 0.f;
+    float be = 0.f, al = 0.f, br = 0.f, bi = 0.f;
     if (live) {
       const int64_t n = (int64_t)j * nlx + i;
       be = betaG[n];
@@ -101,20 +96,15 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
       if (j == 0 && ifS) { br += (float)(a.wxs[i] * lamL[2 * (2 * a.NE + i)]); bi += (float)(a.wxs[i] * lamL[2 * (2 * a.NE + i) + 1]); }
       if (j == NY - 1 && ifN) { br += (float)(a.wxs[i] * lamL[2 * (3 * a.NE + i)]); bi += (float)(a.wxs[i] * lamL[2 * (3 * a.NE + i) + 1]); }
     }
-    const int ay = j % P, ey = j / P;
-    const double wy = a.hy2 * ((ey < a.sye ? a.w[ay] : 0.0) + (ay == 0 && ey >= 1 ? a.w[P] : 0.0));
-    bet[r] = (float)(be * wx_lane * wy);  // beta' = beta Wx Wy
+    bet[r] = (float)(be * wx_lane * x.wyr[j]);  // beta' = beta Wx Wy
     const float fbr = be * br, fbi = be * bi;
     if (SRC) {
       bbr[r] = fbr;
       bbi[r] = fbi;
     }
-    if (j == 0 || j == NY - 1) {
-      alE = al;
-      bEr = SRC ? 0.f : fbr;
-      bEi = SRC ? 0.f : fbi;
-    } else if (slot < 2) {  // the shared row is written by both bands with the same value
-      ecg[j * 2 + slot] = make_float4(al - 1.f, SRC ? 0.f : fbr, SRC ? 0.f : fbi, 0.f);
+    if (j == 0 || j == NY - 1) { alE = al; bEr = SRC ? 0.f : fbr; bEi = SRC ? 0.f : fbi; }
+    if (j > 0 && j < NY - 1) {
+      if (slot < 2) ecg[j * 2 + slot] = make_float4(al - 1.f, SRC ? 0.f : fbr, SRC ? 0.f : fbi, 0.f);
     }
   }
   __syncwarp();
@@ -123,13 +113,7 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
   const float sigma = (float)a.sigma, omega = (float)a.omega;
   const float cpi = (float)a.cpi, spi = (float)a.spi, scale = (float)a.two_over_nt;
   const float sy = x.sy;
-  // first / last subdomain row: the one-element row is 2 x the two-element row
-  // (w_0 = w_P; the missing side's halo is zero) minus the missing element's
-  // diagonal term (see the cluster-of-bands kernel)
-  const float kc_first = kYRows.c[P - 1][P + 1][P];
-  const float kc_last = kYRows.c[P - 1][0][P];
-  const int nout = last ? NR : NR - 1;  // rows this band outputs and counts
-  // exchange buffer layout: [parity][band][side 0 = rows 1..P, 1 = rows RB-P..RB-1][P][32]
+  // exchange buffer layout: [parity][band][side 0 = first P rows, 1 = last P rows][P][32]
   auto xb = [&](int par, int band, int side, int k) -> float& {
     return xbuf[(((par * H + band) * 2 + side) * P + k) * 32 + lane];
   };
@@ -162,42 +146,41 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
       const float4 tn = tab[nu + 1];  // prefetch (the table has N_t + 1 entries)
 #pragma unroll
       for (int r = 0; r < NR; ++r) p[r] += sigma * pd[r];
+      if (HAS_LO) {
 #pragma unroll
-      for (int k = 0; k < P; ++k) {
-        xb(cur, B, 0, k) = p[1 + k];
-        xb(cur, B, 1, k) = p[RB - P + k];
+        for (int k = 0; k < P; ++k) xb(cur, B, 0, k) = p[k];
+      }
+      if (HAS_HI) {
+#pragma unroll
+        for (int k = 0; k < P; ++k) xb(cur, B, 1, k) = p[NR - P + k];
       }
       group_barrier(bar_id, H * 32);
       float lo[P], hi[P];
 #pragma unroll
       for (int k = 0; k < P; ++k) {
-        lo[k] = first ? 0.f : xb(cur, first ? 0 : B - 1, 1, k);  // rows J0-P+k
-        hi[k] = last ? 0.f : xb(cur, last ? 0 : B + 1, 0, k);    // rows J0+NR+k
+        lo[k] = HAS_LO ? xb(cur, B - 1, 1, k) : 0.f;  // rows J0-P+k
+        hi[k] = HAS_HI ? xb(cur, B + 1, 0, k) : 0.f;  // rows J1+k
       }
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         const int j = J0 + r;
-        // (A p)_j / (Wx Wy): y taps of the row's class (element-boundary rows
-        // with both elements), x part by shuffles
-        const int a_r = r % P;
-        const int cls = a_r == 0 ? P : a_r;
+        // (A p)_j / (Wx Wy): y taps (registers and halo rows, compile-time
+        // coefficients times 4/hy^2), x part by shuffles
         float Y = 0.f;
 #pragma unroll
         for (int t = -P; t <= P; ++t) {
-          if (a_r == 0 || (a_r + t >= 0 && a_r + t <= P)) {
-            const int rr = r + t;
-            const float v = rr < 0 ? lo[rr + P] : rr >= NR ? hi[rr - NR] : p[rr];
-            Y += kYRows.c[P - 1][cls][t + P] * v;
+          const int jj = j + t;
+          if (warp_sweep::tap(P, SY, j, t) && jj >= 0 && jj < NY) {
+            const float v = (jj < J0) ? lo[jj - (J0 - P)] : (jj >= J1) ? hi[jj - J1] : p[jj - J0];
+            Y += kYRows.c[P - 1][gllc::row_class(P, SY, j)][t + P] * v;
           }
         }
-        if (r == 0 && first) Y = 2.f * Y - kc_first * p[r];
-        if (r == NR - 1 && last) Y = 2.f * Y - kc_last * p[r];
         const float Ap = xr.apply(p[r], lane) + sy * Y;
-        float f = pd[r] - bet[r] * Ap;
-        if ((r == 0 && first) || (r == NR - 1 && last)) {
-          f += (alE - 1.f) * pd[r] + bEr * tb.x + bEi * tb.y;
+        float f;
+        if (j == 0 || j == NY - 1) {
+          f = alE * pd[r] - bet[r] * Ap + bEr * tb.x + bEi * tb.y;
         } else {
-          f = edge_fix(f, pd[r], &ecg[j * 2 + (slot & 1)], slot < 2, tb.x, tb.y);
+          f = edge_fix(pd[r] - bet[r] * Ap, pd[r], &ecg[j * 2 + (slot & 1)], slot < 2, tb.x, tb.y);
         }
         if (SRC) f += bbr[r] * tb.x + bbi[r] * tb.y;
         pd[r] = f;
@@ -220,12 +203,10 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
       double dn = 0.0, un = 0.0;
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
-        if (r < nout) {  // the shared row counts once
-          const float2 o = uo[r * 32 + lane];
-          const double dr = (double)vre[r] - (double)o.x, di = (double)vim[r] - (double)o.y;
-          dn += dr * dr + di * di;
-          un += (double)vre[r] * vre[r] + (double)vim[r] * vim[r];
-        }
+        const float2 o = uo[r * 32 + lane];
+        const double dr = (double)vre[r] - (double)o.x, di = (double)vim[r] - (double)o.y;
+        dn += dr * dr + di * di;
+        un += (double)vre[r] * vre[r] + (double)vim[r] * vim[r];
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -242,12 +223,11 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
     }
   }
 
-  // ---- outputs (a band's last row is the next band's first: written by that band)
+  // ---- outputs
   bool bad = false;
   if (live) {
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-      if (r >= nout) break;
       if (!isfinite(vre[r]) || !isfinite(vim[r])) bad = true;
       if (a.u_sub) {
         const int64_t n = (int64_t)l * nn + (int64_t)(J0 + r) * nlx + i;
@@ -257,7 +237,7 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
     }
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.flags, 1);
-  if (first && lane == 0 && a.wh_iter_max) {
+  if (B == 0 && lane == 0 && a.wh_iter_max) {
     atomicMax(a.wh_iter_max, m_done);
     atomicAdd(a.wh_iter_sum, (unsigned long long)m_done);
   }
@@ -268,8 +248,8 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
     const int len = (e < 2) ? NY : nlx;
     double* dst;
     if (iface) {
-      const int rn = (e == 0) ? l - 1 : (e == 1) ? l + 1 : (e == 2) ? l - a.Sx : l + a.Sx;
-      dst = a.lam_out + 2 * (((int64_t)rn * 4 + (e ^ 1)) * NE + t);
+      const int r = (e == 0) ? l - 1 : (e == 1) ? l + 1 : (e == 2) ? l - a.Sx : l + a.Sx;
+      dst = a.lam_out + 2 * (((int64_t)r * 4 + (e ^ 1)) * NE + t);
     } else {
       dst = a.lam_out + 2 * (((int64_t)l * 4 + e) * NE + t);
     }
@@ -283,13 +263,13 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
       dst[1] = 0.0;
     }
   };
-  if (first) {  // S edge: row 0
+  if (B == 0) {  // S edge: row 0
     for (int t = lane; t < NE; t += 32) {
       const bool mine = t == lane && live;
       put(2, t, mine, mine ? (double)vre[0] : 0.0, mine ? (double)vim[0] : 0.0);
     }
   }
-  if (last) {  // N edge: row NY-1
+  if (B == H - 1) {  // N edge: row NY-1
     for (int t = lane; t < NE; t += 32) {
       const bool mine = t == lane && live;
       put(3, t, mine, mine ? (double)vre[NR - 1] : 0.0, mine ? (double)vim[NR - 1] : 0.0);
@@ -298,12 +278,11 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
   if (lane == 0 || lane == nlx - 1) {  // W / E edges: this band's rows
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-      if (r >= nout) break;
       if (lane == 0) put(0, J0 + r, true, (double)vre[r], (double)vim[r]);
       if (lane == nlx - 1) put(1, J0 + r, true, (double)vre[r], (double)vim[r]);
     }
   }
-  if (first && lane == 0) {
+  if (B == 0 && lane == 0) {
     for (int t = NY; t < NE; ++t) {
       put(0, t, false, 0.0, 0.0);
       put(1, t, false, 0.0, 0.0);
@@ -317,13 +296,20 @@ __global__ void __launch_bounds__(H * 32, 7) sweep_band_kernel(const __grid_cons
   constexpr int NY = S::NY;
   __shared__ float xbuf_all[S::G][2 * H * 2 * P * 32];
   __shared__ float4 ec_all[S::G][NY * 2];
-  __shared__ float2 uold_all[H][S::NR * 32];
+  __shared__ float2 uold_all[H][S::RB * 32];
   __shared__ double red_all[S::G][2 * H];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = w / H, b = w % H;
   const int l = blockIdx.x * S::G + g;
   if (l >= x.L) return;  // the whole group leaves together (all H warps share l)
-  band_body<P, SY, SRC, H>(x, l, g, lane, b, xbuf_all[g], ec_all[g], uold_all[w], red_all[g]);
+  float* xbuf = xbuf_all[g];
+  float4* ecg = ec_all[g];
+  float2* uo = uold_all[w];
+  double* red = red_all[g];
+  if (b == 0) band_body<P, SY, SRC, H, 0>(x, l, g, lane, xbuf, ecg, uo, red);
+  else if (b == 1) band_body<P, SY, SRC, H, (H > 1 ? 1 : 0)>(x, l, g, lane, xbuf, ecg, uo, red);
+  else if (b == 2) band_body<P, SY, SRC, H, (H > 2 ? 2 : 0)>(x, l, g, lane, xbuf, ecg, uo, red);
+  else band_body<P, SY, SRC, H, (H > 3 ? 3 : 0)>(x, l, g, lane, xbuf, ecg, uo, red);
 }
 
 }  // namespace band_sweep
