@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--wh-iters", type=int, default=20, help="WaveHoltz iterations per sweep")
     ap.add_argument("--max-sweeps", type=int, default=5000)
     ap.add_argument("--max-refine", type=int, default=20)
+    ap.add_argument("--robin", default="0,1", help="interface condition d_n + k (eta - i zeta): 'eta,zeta'")
     ap.add_argument("--workload", choices=["cfg1", "cfg2", "cfg3", "cfg3s"], default="cfg2",
                     help="cfg2 is the benchmark workload; cfg1/cfg3 are reported separately; cfg3s is the "
                          "cfg3 physics and subdomain shape on a 256x256 mesh (for profiling)")
@@ -212,6 +213,9 @@ def run_ours(args):
 
     wl = workload(args.workload)
     case = Case(wl, device=local)
+    robin = [float(v) for v in args.robin.split(",")]
+    if robin != [0.0, 1.0]:
+        hz.hz_problem_set(case.pr, hz.HZ_TRANSMISSION, np.array(robin))
     n = case.n
     stream = torch.cuda.current_stream()
     opts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, inner_tol=1e-2, wh_iters=args.wh_iters,
@@ -333,6 +337,7 @@ def run_ours(args):
                        "subdomains": f"{wl.nx // wl.sub_nx}x{wl.ny // wl.sub_ny} of {wl.sub_nx}x{wl.sub_ny}",
                        "omega": wl.omega, "nt": nt, "wh_iters": opts.wh_iters, "tol": TOL,
                        "outer": "GMRES(60) in FP64 defect correction", "l2": "flushed (256 MB write) before each step",
+                       "transmission": {"eta": robin[0], "zeta": robin[1]},
                        "parallelism": f"{world} independent solves (one per GPU)"},
             "time_to_tol_s": {"fp32_refine": elapsed / args.steps, "fp64": fp64["seconds"] if fp64 else None},
             "fp64_solve": fp64,

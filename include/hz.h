@@ -85,9 +85,15 @@ typedef enum {
   HZ_WAVE_SPEED = 0, /* n real values, finite and > 0 (c at every node) */
   HZ_OMEGA = 1,      /* 1 real value > 0 */
   HZ_SOURCE = 2,     /* n complex values (f at every node) */
-  HZ_BOUNDARY = 3    /* 2*(nx*P+1) + 2*(ny*P+1) complex values of g on the outer
+  HZ_BOUNDARY = 3,   /* 2*(nx*P+1) + 2*(ny*P+1) complex values of g on the outer
                         edges in the order S, E, N, W, each along increasing x
                         (S, N) or y (E, W); corners carry one value per edge */
+  HZ_TRANSMISSION = 4 /* 2 real values (eta >= 0, zeta > 0): the interface condition
+                        B = d_n + k (eta - i zeta) used between subdomains (default
+                        eta = 0, zeta = 1: B = d_n - i k, Sec. 3); eta > 0 adds a
+                        boundary mass that damps evanescent interface modes (the
+                        improved transmission conditions of Sec. 8).  The converged
+                        solution does not depend on it, only the iteration count. */
 } hz_field;
 
 typedef struct {

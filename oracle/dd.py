@@ -15,6 +15,13 @@ cycle of Algorithm 1 runs on every subdomain independently, Sec. 6):
   subdomain, Algorithm 1's loop order.
 * Transmission update (eq. (lambda-iteration), Algorithm 1 last step):
   lambda_{r,l} <- -lambda_{l,r} - 2 i k u_l on Gamma_{l,r}.
+* Optional generalised transmission condition (the improved transmission
+  conditions the paper names as future work, Sec. 8): B = d_n + k (eta - i zeta)
+  on interfaces; eta = 0, zeta = 1 is the paper's condition.  In the subdomain
+  operator the interface edges then carry zeta times the impedance damping
+  and a boundary mass w eta <c^-1 phi_j, phi_i> (time domain:
+  d_n u + (zeta/c) u_t + (w eta / c) u), and the update reads
+  lambda_{r,l} <- -lambda_{l,r} + 2 k (eta - i zeta) u_l.
 
 Readings of the paper taken here (each pinned by a test):
   1. lambda update sign -2ik (the paper prints +2ik; with outward normals and
@@ -53,8 +60,9 @@ class Problem:
     """One Helmholtz problem on a Mesh: nodal wave speed c (NY,NX), omega,
     nodal source f (NY,NX) complex, outer boundary data g (dict S,E,N,W)."""
 
-    def __init__(self, mesh: Mesh, c, omega, f, g=None):
+    def __init__(self, mesh: Mesh, c, omega, f, g=None, robin=(0.0, 1.0)):
         self.mesh = mesh
+        self.eta, self.zeta = float(robin[0]), float(robin[1])
         self.c = np.asarray(c, dtype=float).reshape(mesh.NY, mesh.NX)
         self.omega = float(omega)
         self.f = np.asarray(f, dtype=complex).reshape(mesh.NY, mesh.NX)
@@ -116,15 +124,6 @@ class Problem:
         self.Wxs = m.lumped_1d(m.sub_nx, m.hx)
         self.Wys = m.lumped_1d(m.sub_ny, m.hy)
         Ws = np.outer(self.Wys, self.Wxs)
-        Hws = np.zeros((m.nly, m.nlx))
-        Hws[0, :] += self.Wxs
-        Hws[-1, :] += self.Wxs
-        Hws[:, 0] += self.Wys
-        Hws[:, -1] += self.Wys
-        self.c_sub = self.c[self.gJ, self.gI]
-        self.M_sub = Ws[None] / self.c_sub**2
-        self.H_sub = Hws[None] / self.c_sub
-        self.share = Ws[None] / self.W2[self.gJ, self.gI]  # lumped-mass share of each copy
         # neighbours and interface flags per edge
         self.nbr = -np.ones((L, 4), dtype=int)
         for l in range(L):
@@ -137,6 +136,18 @@ class Problem:
                 self.nbr[l, EDGE_S] = l - m.Sx
             if sy < m.Sy - 1:
                 self.nbr[l, EDGE_N] = l + m.Sx
+        # edge quadrature weights, split into outer-boundary and interface edges
+        Hout = np.zeros((L, m.nly, m.nlx))
+        Hif = np.zeros((L, m.nly, m.nlx))
+        for e in range(4):
+            rows, cols, wts = self.edge_nodes(e)
+            for l in range(L):
+                (Hif if self.nbr[l, e] >= 0 else Hout)[l, rows, cols] += wts
+        self.c_sub = self.c[self.gJ, self.gI]
+        self.M_sub = Ws[None] / self.c_sub**2
+        self.H_sub = (Hout + self.zeta * Hif) / self.c_sub          # damping: outer impedance, zeta on interfaces
+        self.Hm_sub = self.omega * self.eta * Hif / self.c_sub      # interface boundary mass (eta)
+        self.share = Ws[None] / self.W2[self.gJ, self.gI]  # lumped-mass share of each copy
 
     def edge_nodes(self, e):
         """(rows, cols, weights) of subdomain edge e in local node indices."""
@@ -217,7 +228,7 @@ class Problem:
             for l in sel[self.nbr[sel, e] >= 0]:
                 r = self.nbr[l, e]
                 k = w / self.c_sub[l, rows, cols]
-                lam_out[r, OPPOSITE[e], :n] = -lam_in[l, e, :n] - 2j * k * u[l, rows, cols]
+                lam_out[r, OPPOSITE[e], :n] = -lam_in[l, e, :n] + 2 * k * (self.eta - 1j * self.zeta) * u[l, rows, cols]
         if want_u:
             return lam_out, u, iters
         return lam_out
@@ -242,7 +253,7 @@ class Problem:
         if not hasattr(self, "_A_sub"):
             self._A_sub = stiffness_matrix(m.P, m.D, m.w, m.hx, m.hy, m.sub_nx, m.sub_ny)
         w = self.omega
-        d = -1j * w * self.H_sub[l].ravel() - w * w * self.M_sub[l].ravel()
+        d = self.Hm_sub[l].ravel() - 1j * w * self.H_sub[l].ravel() - w * w * self.M_sub[l].ravel()
         return (self._A_sub + sp.diags(d)).tocsc()
 
     def direct_sub(self, b, sel):
@@ -264,6 +275,7 @@ class Problem:
         Returns (u, iterations per subdomain)."""
         w = self.omega
         alpha, beta, sigma = self.leapfrog_coeffs(Nt, subs)
+        Hm = self.Hm_sub if subs is None else self.Hm_sub[subs]
         c0 = -0.25 + 0.25 * math.tan(math.pi / Nt) ** 2
 
         def kappa(nu):
@@ -282,7 +294,7 @@ class Problem:
             v = kappa(0) * p + (1j / w) * kappa(0.5) * pd
             for nu in range(1, last + 1):
                 p = p + sigma * pd
-                Ap = self.apply_A_sub(p)
+                Ap = self.apply_A_sub(p) + Hm * p  # interface boundary mass (zero unless eta != 0)
                 force = (b * np.exp(-2j * math.pi * nu / Nt)).real
                 pd = alpha * pd + beta * (-Ap + force)
                 v = v + kappa(nu) * p + (1j / w) * kappa(nu + 0.5) * pd

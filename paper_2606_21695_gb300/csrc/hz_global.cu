@@ -54,7 +54,12 @@ __global__ void prepare_kernel(const __grid_constant__ PrepArgs a) {
     const int64_t I = (int64_t)sxi * a.snxP + i, J = (int64_t)syi * a.snyP + j;
     const double c = a.c[J * a.NXg + I];
     const double M = a.wxs[i] * a.wys[j] / (c * c);
-    const double Hw = ((j == 0 || j == a.nly - 1) ? a.wxs[i] : 0.0) + ((i == 0 || i == a.nlx - 1) ? a.wys[j] : 0.0);
+    // impedance damping on every subdomain edge: weight 1 on the outer
+    // boundary, zeta on interfaces (the interface condition's d_t part)
+    const double fS = syi > 0 ? a.zeta : 1.0, fN = syi < a.Sy - 1 ? a.zeta : 1.0;
+    const double fW = sxi > 0 ? a.zeta : 1.0, fE = sxi < a.Sx - 1 ? a.zeta : 1.0;
+    const double Hw = (j == 0 ? fS * a.wxs[i] : 0.0) + (j == a.nly - 1 ? fN * a.wxs[i] : 0.0) +
+                      (i == 0 ? fW * a.wys[j] : 0.0) + (i == a.nlx - 1 ? fE * a.wys[j] : 0.0);
     const double H = Hw / c;
     const double den = M + a.theta * H;
     const double be = a.sigma / den;

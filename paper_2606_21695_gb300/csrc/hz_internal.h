@@ -73,6 +73,7 @@ struct SweepArgs {
   int Nt, m_wh;
   double wh_tol, sigma, omega, cpi, spi, two_over_nt;
   double kxs, kys, hx2, hy2;  // 2/hx, 2/hy, hx/2, hy/2
+  double eta, zeta;           // interface condition d_n + k (eta - i zeta)
   double Kref[(kMaxP + 1) * (kMaxP + 1)];
   float Kref32[(kMaxP + 1) * (kMaxP + 1)];
   double w[kMaxP + 1];
@@ -135,6 +136,7 @@ inline hz_status launch_sweep(bool fp32, int P, const SweepArgs& a, int L, cudaS
 struct PrepArgs {
   int nlx, nly, NE, Sx, Sy, NXg, snxP, snyP;
   double theta, sigma, omega;
+  double zeta;          // interface damping factor (outer edges: 1)
   const double* c;      // global
   const double* wxs;
   const double* wys;

@@ -30,6 +30,7 @@ struct hz_problem_s {
   int device = 0;
   cudaStream_t stream = nullptr;
   double omega = 0.0, cmax = 0.0, sigma = 0.0;
+  double robin_eta = 0.0, robin_zeta = 1.0;  // interface condition d_n + k (eta - i zeta)
   bool has_c = false, has_omega = false;
   int version = 0;            // bumped on every field change
   int prepared_nt = 0, prepared_version = -1;

@@ -151,6 +151,7 @@ hz_status prepare(Problem& pr, int nt, cudaStream_t st) {
   a.theta = std::tan(w * dt / 2.0) / w;
   a.sigma = std::sin(w * dt / 2.0) / (w / 2.0);
   a.omega = w;
+  a.zeta = pr.robin_zeta;
   a.c = pr.c.as<double>();
   a.wxs = pr.wxs.as<double>();
   a.wys = pr.wys.as<double>();
@@ -299,6 +300,8 @@ SweepArgs make_sweep_args(Problem& pr, bool fp32, int nt, int m_wh, double wh_to
   a.kys = 2.0 / g.hy;
   a.hx2 = g.hx / 2.0;
   a.hy2 = g.hy / 2.0;
+  a.eta = pr.robin_eta;
+  a.zeta = pr.robin_zeta;
   for (size_t k = 0; k < g.Kref.size(); ++k) {
     a.Kref[k] = g.Kref[k];
     a.Kref32[k] = (float)g.Kref[k];
@@ -911,6 +914,7 @@ int64_t field_count(const Geom& g, hz_field f) {
     case HZ_OMEGA: return 1;
     case HZ_SOURCE: return g.n;
     case HZ_BOUNDARY: return 2 * (int64_t)g.NXg + 2 * (int64_t)g.NYg;
+    case HZ_TRANSMISSION: return 2;
   }
   return -1;
 }
@@ -950,6 +954,11 @@ hz_status set_field_host(Problem& pr, hz_field field, const double* data, int64_
     case HZ_BOUNDARY:
       HZ_TRY(pr.gb.ensure(nd * sizeof(double)));
       HZ_CUDA(cudaMemcpy(pr.gb.ptr, data, nd * sizeof(double), cudaMemcpyHostToDevice));
+      break;
+    case HZ_TRANSMISSION:
+      if (!(data[0] >= 0.0) || !(data[1] > 0.0)) return fail(HZ_ERR_INVALID_ARG, "need eta >= 0 and zeta > 0");
+      pr.robin_eta = data[0];
+      pr.robin_zeta = data[1];
       break;
   }
   pr.version++;
@@ -1094,7 +1103,8 @@ hz_status hz_problem_set_device(hz_problem pr, hz_field field, const double* dat
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     HZ_CUDA(cudaMemcpyAsync(tmp.data(), data, nd * sizeof(double), cudaMemcpyDeviceToHost, st));
     HZ_CUDA(cudaStreamSynchronize(st));
-    if (field == HZ_OMEGA || field == HZ_WAVE_SPEED) return set_field_host(*pr, field, tmp.data(), count);
+    if (field == HZ_OMEGA || field == HZ_WAVE_SPEED || field == HZ_TRANSMISSION)
+      return set_field_host(*pr, field, tmp.data(), count);
     if (!all_finite(tmp.data(), nd)) return fail(HZ_ERR_INVALID_ARG, "non-finite input");
     DevBuf& dst = field == HZ_SOURCE ? pr->f : pr->gb;
     HZ_TRY(dst.ensure(nd * sizeof(double)));

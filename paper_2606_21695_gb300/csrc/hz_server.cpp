@@ -64,6 +64,8 @@ hz_status clone_problem(const hz_problem_s& src, std::unique_ptr<hz_problem_s>* 
   pr->device = src.device;
   pr->omega = src.omega;
   pr->cmax = src.cmax;
+  pr->robin_eta = src.robin_eta;
+  pr->robin_zeta = src.robin_zeta;
   pr->has_c = src.has_c;
   pr->has_omega = src.has_omega;
   HZ_CUDA(cudaSetDevice(src.device));

@@ -70,15 +70,17 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
   const float* alphaG = static_cast<const float*>(a.alpha) + (int64_t)l * nn;
   const double* lamL = a.lam_in + (int64_t)l * 4 * a.NE * 2;
   const bool ifW = sxi > 0, ifE = sxi < a.Sx - 1, ifS = syi > 0, ifN = syi < a.Sy - 1;
+  const double* kedgeL = a.kedge + (int64_t)l * 4 * a.NE;
   const int slot = (lane == 0) ? 0 : (lane == nlx - 1) ? 1 : 2;
   constexpr int NB = SRC ? NR : 1;
   float bet[NR];
   float bbr[NB], bbi[NB];
-  float alE = 0.f, bEr = 0.f, bEi = 0.f;  // row 0 (band 0) or row NY-1 (last band)
+  float alE = 0.f, bEr = 0.f, bEi = 0.f, gE = 0.f;  // row 0 (band 0) or row NY-1 (last band)
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
     const int j = J0 + r;
     float be = 0.f, al = 0.f, br = 0.f, bi = 0.f;
+    double hm = 0.0;
     if (live) {
       const int64_t n = (int64_t)j * nlx + i;
       be = betaG[n];
@@ -95,16 +97,22 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
       if (i == nlx - 1 && ifE) { br += (float)(a.wys[j] * lamL[2 * (1 * a.NE + j)]); bi += (float)(a.wys[j] * lamL[2 * (1 * a.NE + j) + 1]); }
       if (j == 0 && ifS) { br += (float)(a.wxs[i] * lamL[2 * (2 * a.NE + i)]); bi += (float)(a.wxs[i] * lamL[2 * (2 * a.NE + i) + 1]); }
       if (j == NY - 1 && ifN) { br += (float)(a.wxs[i] * lamL[2 * (3 * a.NE + i)]); bi += (float)(a.wxs[i] * lamL[2 * (3 * a.NE + i) + 1]); }
+      // interface boundary mass (k w on each interface edge of the node)
+      if (i == 0 && ifW) hm += a.wys[j] * kedgeL[0 * a.NE + j];
+      if (i == nlx - 1 && ifE) hm += a.wys[j] * kedgeL[1 * a.NE + j];
+      if (j == 0 && ifS) hm += a.wxs[i] * kedgeL[2 * a.NE + i];
+      if (j == NY - 1 && ifN) hm += a.wxs[i] * kedgeL[3 * a.NE + i];
     }
+    const float gm = (float)(-(double)be * a.eta * hm);  // gamma = -beta w eta <c^-1 phi, phi>
     bet[r] = (float)(be * wx_lane * x.wyr[j]);  // beta' = beta Wx Wy
     const float fbr = be * br, fbi = be * bi;
     if (SRC) {
       bbr[r] = fbr;
       bbi[r] = fbi;
     }
-    if (j == 0 || j == NY - 1) { alE = al; bEr = SRC ? 0.f : fbr; bEi = SRC ? 0.f : fbi; }
+    if (j == 0 || j == NY - 1) { alE = al; bEr = SRC ? 0.f : fbr; bEi = SRC ? 0.f : fbi; gE = gm; }
     if (j > 0 && j < NY - 1) {
-      if (slot < 2) ecg[j * 2 + slot] = make_float4(al - 1.f, SRC ? 0.f : fbr, SRC ? 0.f : fbi, 0.f);
+      if (slot < 2) ecg[j * 2 + slot] = make_float4(al - 1.f, SRC ? 0.f : fbr, SRC ? 0.f : fbi, gm);
     }
   }
   __syncwarp();
@@ -178,9 +186,9 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
         const float Ap = xr.apply(p[r], lane) + sy * Y;
         float f;
         if (j == 0 || j == NY - 1) {
-          f = alE * pd[r] - bet[r] * Ap + bEr * tb.x + bEi * tb.y;
+          f = alE * pd[r] - bet[r] * Ap + bEr * tb.x + bEi * tb.y + gE * p[r];
         } else {
-          f = edge_fix(pd[r] - bet[r] * Ap, pd[r], &ecg[j * 2 + (slot & 1)], slot < 2, tb.x, tb.y);
+          f = edge_fix(pd[r] - bet[r] * Ap, pd[r], p[r], &ecg[j * 2 + (slot & 1)], slot < 2, tb.x, tb.y);
         }
         if (SRC) f += bbr[r] * tb.x + bbi[r] * tb.y;
         pd[r] = f;
@@ -242,7 +250,6 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
     atomicAdd(a.wh_iter_sum, (unsigned long long)m_done);
   }
   const int NE = a.NE;
-  const double* kedgeL = a.kedge + (int64_t)l * 4 * NE;
   auto put = [&](int e, int t, bool has, double ur, double ui) {
     const bool iface = (e == 0) ? ifW : (e == 1) ? ifE : (e == 2) ? ifS : ifN;
     const int len = (e < 2) ? NY : nlx;
@@ -256,8 +263,9 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
     if (iface && t < len && has) {
       const double kk = kedgeL[e * NE + t];
       const double lr = lamL[2 * (e * NE + t)], li = lamL[2 * (e * NE + t) + 1];
-      dst[0] = -lr + 2.0 * kk * ui;
-      dst[1] = -li - 2.0 * kk * ur;
+      // -lambda + 2 k (eta - i zeta) u  (eta = 0, zeta = 1: -lambda - 2ik u)
+      dst[0] = -lr + 2.0 * kk * (a.eta * ur + a.zeta * ui);
+      dst[1] = -li + 2.0 * kk * (a.eta * ui - a.zeta * ur);
     } else {
       dst[0] = 0.0;
       dst[1] = 0.0;

@@ -97,14 +97,15 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
   const double* lamL = a.lam_in + (int64_t)l * 4 * a.NE * 2;
   const bool ifW = sxi > 0, ifE = sxi < a.Sx - 1, ifS = syi > 0, ifN = syi < a.Sy - 1;
   const bool edge = live && (c == 0 || c == nlx - 1);
+  const double* kedgeL = a.kedge + (int64_t)l * 4 * a.NE;
   constexpr int NB = SRC ? NR : 1;
   float bet[NR];
   float bbr[NB], bbi[NB];
-  float alE = 1.f, bEr = 0.f, bEi = 0.f;  // row 0 (first band) or row NY-1 (last band)
+  float alE = 1.f, bEr = 0.f, bEi = 0.f, gE = 0.f;  // row 0 (first band) or row NY-1 (last band)
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
     const int j = J0 + r;
-    double be = 0.0, al = 1.0, br = 0.0, bi = 0.0;
+    double be = 0.0, al = 1.0, br = 0.0, bi = 0.0, hm = 0.0;
     if (live) {
       const int64_t n = (int64_t)j * nlx + c;
       be = (double)betaG[n];
@@ -121,7 +122,13 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
       if (c == nlx - 1 && ifE) { br += a.wys[j] * lamL[2 * (1 * a.NE + j)]; bi += a.wys[j] * lamL[2 * (1 * a.NE + j) + 1]; }
       if (j == 0 && ifS) { br += a.wxs[c] * lamL[2 * (2 * a.NE + c)]; bi += a.wxs[c] * lamL[2 * (2 * a.NE + c) + 1]; }
       if (j == NY - 1 && ifN) { br += a.wxs[c] * lamL[2 * (3 * a.NE + c)]; bi += a.wxs[c] * lamL[2 * (3 * a.NE + c) + 1]; }
+      // interface boundary mass (k w on each interface edge of the node)
+      if (c == 0 && ifW) hm += a.wys[j] * kedgeL[0 * a.NE + j];
+      if (c == nlx - 1 && ifE) hm += a.wys[j] * kedgeL[1 * a.NE + j];
+      if (j == 0 && ifS) hm += a.wxs[c] * kedgeL[2 * a.NE + c];
+      if (j == NY - 1 && ifN) hm += a.wxs[c] * kedgeL[3 * a.NE + c];
     }
+    const float gm = (float)(-be * a.eta * hm);  // gamma = -beta w eta <c^-1 phi, phi>
     const int ay = j % P, ey = j / P;
     const double wy = a.hy2 * ((ey < a.sye ? a.w[ay] : 0.0) + (ay == 0 && ey >= 1 ? a.w[P] : 0.0));
     bet[r] = (float)(be * wx_lane * wy);  // beta' = beta Wx Wy
@@ -134,8 +141,9 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
       alE = (float)al;
       bEr = SRC ? 0.f : fbr;
       bEi = SRC ? 0.f : fbi;
+      gE = gm;
     } else if (edge) {
-      sm.ecol[j] = make_float4((float)(al - 1.0), SRC ? 0.f : fbr, SRC ? 0.f : fbi, 0.f);
+      sm.ecol[j] = make_float4((float)(al - 1.0), SRC ? 0.f : fbr, SRC ? 0.f : fbi, gm);
     }
   }
   __syncwarp();
@@ -226,9 +234,9 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
         float f = pd[r] - bet[r] * Ap;
         const bool srow = (r == 0 && first) || (r == NR - 1 && last);
         if (srow) {
-          f += (alE - 1.f) * pd[r] + bEr * tb.x + bEi * tb.y;
+          f += (alE - 1.f) * pd[r] + bEr * tb.x + bEi * tb.y + gE * p[r];
         } else {
-          f = edge_fix(f, pd[r], &sm.ecol[j], edge, tb.x, tb.y);
+          f = edge_fix(f, pd[r], p[r], &sm.ecol[j], edge, tb.x, tb.y);
         }
         if (SRC) f += bbr[r] * tb.x + bbi[r] * tb.y;
         pd[r] = f;
@@ -269,7 +277,6 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
     atomicAdd(a.wh_iter_sum, (unsigned long long)m_wh);
   }
   const int NE = a.NE;
-  const double* kedgeL = a.kedge + (int64_t)l * 4 * NE;
   auto put = [&](int e, int t, bool has, double ur, double ui) {
     const bool iface = (e == 0) ? ifW : (e == 1) ? ifE : (e == 2) ? ifS : ifN;
     const int len = (e < 2) ? NY : nlx;
@@ -283,8 +290,9 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
     if (iface && t < len && has) {
       const double kk = kedgeL[e * NE + t];
       const double lr = lamL[2 * (e * NE + t)], li = lamL[2 * (e * NE + t) + 1];
-      dst[0] = -lr + 2.0 * kk * ui;
-      dst[1] = -li - 2.0 * kk * ur;
+      // -lambda + 2 k (eta - i zeta) u  (eta = 0, zeta = 1: -lambda - 2ik u)
+      dst[0] = -lr + 2.0 * kk * (a.eta * ur + a.zeta * ui);
+      dst[1] = -li + 2.0 * kk * (a.eta * ui - a.zeta * ur);
     } else {
       dst[0] = 0.0;
       dst[1] = 0.0;

@@ -114,16 +114,17 @@ __global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_k
   const double* lamL = a.lam_in + (int64_t)l * 4 * a.NE * 2;
   const bool ifW = sxi > 0, ifE = sxi < a.Sx - 1, ifS = syi > 0, ifN = syi < a.Sy - 1;
   constexpr int NR = SRC ? RY : 1;
-  float bet[RY], alp[NR], bbr[NR], bbi[NR];
+  const double* kedgeE = a.kedge + (int64_t)l * 4 * a.NE;
+  float bet[RY], alp[NR], bbr[NR], bbi[NR], gam[NR];
   // no source: first / last node row of the subdomain (all columns), and the edge columns
-  float al0 = 1.f, b0r = 0.f, b0i = 0.f, alN = 1.f, bNr = 0.f, bNi = 0.f;
+  float al0 = 1.f, b0r = 0.f, b0i = 0.f, g0 = 0.f, alN = 1.f, bNr = 0.f, bNi = 0.f, gN = 0.f;
   const int slot = (i == 0) ? 0 : (i == nlx - 1) ? 1 : 2;
   const bool edge_col = active && slot < 2;
 #pragma unroll
   for (int r = 0; r < RY; ++r) {
     const int j = j0 + r;
     const bool live = active && (j < nly);
-    double be = 0.0, al = 0.0, br = 0.0, bi = 0.0;
+    double be = 0.0, al = 0.0, br = 0.0, bi = 0.0, hm = 0.0;
     if (live) {
       const int64_t n = (int64_t)j * nlx + i;
       be = (double)betaG[n];
@@ -140,17 +141,24 @@ __global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_k
       if (i == nlx - 1 && ifE) { br += a.wys[j] * lamL[2 * (1 * a.NE + j)]; bi += a.wys[j] * lamL[2 * (1 * a.NE + j) + 1]; }
       if (j == 0 && ifS) { br += a.wxs[i] * lamL[2 * (2 * a.NE + i)]; bi += a.wxs[i] * lamL[2 * (2 * a.NE + i) + 1]; }
       if (j == nly - 1 && ifN) { br += a.wxs[i] * lamL[2 * (3 * a.NE + i)]; bi += a.wxs[i] * lamL[2 * (3 * a.NE + i) + 1]; }
+      // interface boundary mass (k w on each interface edge of the node)
+      if (i == 0 && ifW) hm += a.wys[j] * kedgeE[0 * a.NE + j];
+      if (i == nlx - 1 && ifE) hm += a.wys[j] * kedgeE[1 * a.NE + j];
+      if (j == 0 && ifS) hm += a.wxs[i] * kedgeE[2 * a.NE + i];
+      if (j == nly - 1 && ifN) hm += a.wxs[i] * kedgeE[3 * a.NE + i];
     }
+    const float gm = (float)(-be * a.eta * hm);  // gamma = -beta w eta <c^-1 phi, phi>
     bet[r] = (float)be;
     if (SRC) {
       alp[r] = (float)al;
       bbr[r] = (float)(be * br);
       bbi[r] = (float)(be * bi);
+      gam[r] = gm;
     } else if (live) {
-      if (j == 0) { al0 = (float)al; b0r = (float)(be * br); b0i = (float)(be * bi); }
-      if (j == nly - 1) { alN = (float)al; bNr = (float)(be * br); bNi = (float)(be * bi); }
+      if (j == 0) { al0 = (float)al; b0r = (float)(be * br); b0i = (float)(be * bi); g0 = gm; }
+      if (j == nly - 1) { alN = (float)al; bNr = (float)(be * br); bNi = (float)(be * bi); gN = gm; }
       if (j > 0 && j < nly - 1 && slot < 2)
-        ecol[j * 2 + slot] = make_float4((float)(al - 1.0), (float)(be * br), (float)(be * bi), 0.f);
+        ecol[j * 2 + slot] = make_float4((float)(al - 1.0), (float)(be * br), (float)(be * bi), gm);
     }
   }
 
@@ -246,17 +254,17 @@ __global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_k
         }
         const float Ap = wy[r] * sx + wxy * sy[r];
         if (SRC) {
-          pd[r] = alp[r] * pd[r] - bet[r] * Ap + bbr[r] * tb.x + bbi[r] * tb.y;
+          pd[r] = alp[r] * pd[r] - bet[r] * Ap + bbr[r] * tb.x + bbi[r] * tb.y + gam[r] * p[r];
         } else {
           const int j = j0 + r;
           float f = pd[r] - bet[r] * Ap;
           if (r % P == 0) {  // only element-boundary rows can be the first or last row
-            if (j == 0) f += (al0 - 1.f) * pd[r] + b0r * tb.x + b0i * tb.y;
-            if (j == nly - 1) f += (alN - 1.f) * pd[r] + bNr * tb.x + bNi * tb.y;
+            if (j == 0) f += (al0 - 1.f) * pd[r] + b0r * tb.x + b0i * tb.y + g0 * p[r];
+            if (j == nly - 1) f += (alN - 1.f) * pd[r] + bNr * tb.x + bNi * tb.y + gN * p[r];
           }
           if (edge_col && j > 0 && j < nly - 1) {
             const float4 e = ecol[j * 2 + slot];
-            f += e.x * pd[r] + e.y * tb.x + e.z * tb.y;
+            f += e.x * pd[r] + e.y * tb.x + e.z * tb.y + e.w * p[r];
           }
           pd[r] = f;
         }
@@ -366,8 +374,9 @@ __global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_k
       const double ur = (double)su[2 * (gj * BW + li)], ui = (double)su[2 * (gj * BW + li) + 1];
       const double kk = kedgeL[e * NE + tt];
       const double lr = lamL[2 * (e * NE + tt)], li2 = lamL[2 * (e * NE + tt) + 1];
-      dst[0] = -lr + 2.0 * kk * ui;
-      dst[1] = -li2 - 2.0 * kk * ur;
+      // -lambda + 2 k (eta - i zeta) u  (eta = 0, zeta = 1: -lambda - 2ik u)
+      dst[0] = -lr + 2.0 * kk * (a.eta * ur + a.zeta * ui);
+      dst[1] = -li2 + 2.0 * kk * (a.eta * ui - a.zeta * ur);
     } else {
       dst[0] = 0.0;
       dst[1] = 0.0;

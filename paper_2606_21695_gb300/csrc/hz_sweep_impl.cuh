@@ -136,12 +136,13 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(const __grid_constant__ Swe
   const Real* alphaG = static_cast<const Real*>(a.alpha) + (int64_t)l * nn;
   const double* lamL = a.lam_in + (int64_t)l * 4 * a.NE * 2;
   const bool ifW = sxi > 0, ifE = sxi < a.Sx - 1, ifS = syi > 0, ifN = syi < a.Sy - 1;
-  Real bet[RY], alp[RY], bbr[RY], bbi[RY];
+  const double* kedgeE = a.kedge + (int64_t)l * 4 * a.NE;
+  Real bet[RY], alp[RY], bbr[RY], bbi[RY], gam[RY];
 #pragma unroll
   for (int r = 0; r < RY; ++r) {
     const int j = j0 + r;
     const bool live = active && (j < nly);
-    double be = 0.0, al = 0.0, br = 0.0, bi = 0.0;
+    double be = 0.0, al = 0.0, br = 0.0, bi = 0.0, hm = 0.0;
     if (live) {
       const int64_t n = (int64_t)j * nlx + i;
       be = (double)betaG[n];
@@ -158,7 +159,13 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(const __grid_constant__ Swe
       if (i == nlx - 1 && ifE) { br += a.wys[j] * lamL[2 * (1 * a.NE + j)]; bi += a.wys[j] * lamL[2 * (1 * a.NE + j) + 1]; }
       if (j == 0 && ifS) { br += a.wxs[i] * lamL[2 * (2 * a.NE + i)]; bi += a.wxs[i] * lamL[2 * (2 * a.NE + i) + 1]; }
       if (j == nly - 1 && ifN) { br += a.wxs[i] * lamL[2 * (3 * a.NE + i)]; bi += a.wxs[i] * lamL[2 * (3 * a.NE + i) + 1]; }
+      // interface boundary mass (k w on each interface edge of the node)
+      if (i == 0 && ifW) hm += a.wys[j] * kedgeE[0 * a.NE + j];
+      if (i == nlx - 1 && ifE) hm += a.wys[j] * kedgeE[1 * a.NE + j];
+      if (j == 0 && ifS) hm += a.wxs[i] * kedgeE[2 * a.NE + i];
+      if (j == nly - 1 && ifN) hm += a.wxs[i] * kedgeE[3 * a.NE + i];
     }
+    gam[r] = Real(-be * a.eta * hm);  // gamma = -beta w eta <c^-1 phi, phi>
     bet[r] = Real(be);
     alp[r] = Real(al);
     bbr[r] = Real(be * br);
@@ -244,7 +251,7 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(const __grid_constant__ Swe
           sx += kx[tt] * row[tt];
         }
         const Real Ap = wy[r] * sx + wxy * sy[r];
-        pd[r] = round16(alp[r] * pd[r] - bet[r] * Ap + bbr[r] * tb.x + bbi[r] * tb.y, a.round_mode);
+        pd[r] = round16(alp[r] * pd[r] - bet[r] * Ap + bbr[r] * tb.x + bbi[r] * tb.y + gam[r] * p[r], a.round_mode);
         vre[r] += tb.z * p[r];
         vim[r] += tb.w * pd[r];
       }
@@ -329,9 +336,9 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(const __grid_constant__ Swe
         const double ur = (double)su[2 * n], ui = (double)su[2 * n + 1];
         const double kk = kedgeL[e * NE + tt];
         const double lr = lamL[2 * (e * NE + tt)], li = lamL[2 * (e * NE + tt) + 1];
-        // -lambda - 2 i k u  =  (-lr + 2 k ui) + i (-li - 2 k ur)
-        dst[0] = -lr + 2.0 * kk * ui;
-        dst[1] = -li - 2.0 * kk * ur;
+        // -lambda + 2 k (eta - i zeta) u  (eta = 0, zeta = 1: -lambda - 2ik u)
+        dst[0] = -lr + 2.0 * kk * (a.eta * ur + a.zeta * ui);
+        dst[1] = -li + 2.0 * kk * (a.eta * ui - a.zeta * ur);
       } else {
         dst[0] = 0.0;
         dst[1] = 0.0;

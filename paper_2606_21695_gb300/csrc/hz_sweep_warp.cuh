@@ -70,13 +70,14 @@ __device__ __forceinline__ void warp_body(const WarpSweepArgs& x, int l, float4 
   const float* alphaG = static_cast<const float*>(a.alpha) + (int64_t)l * nn;
   const double* lamL = a.lam_in + (int64_t)l * 4 * a.NE * 2;
   const bool ifW = sxi > 0, ifE = sxi < a.Sx - 1, ifS = syi > 0, ifN = syi < a.Sy - 1;
+  const double* kedgeL = a.kedge + (int64_t)l * 4 * a.NE;
   const int slot = (lane == 0) ? 0 : (lane == nlx - 1) ? 1 : 2;
   float bet[NY];
   float bbr[NB], bbi[NB];
-  float al0 = 0.f, alN = 0.f, b0r = 0.f, b0i = 0.f, bNr = 0.f, bNi = 0.f;
+  float al0 = 0.f, alN = 0.f, b0r = 0.f, b0i = 0.f, bNr = 0.f, bNi = 0.f, g0 = 0.f, gN = 0.f;
 #pragma unroll
   for (int j = 0; j < NY; ++j) {
-    double be = 0.0, al = 0.0, br = 0.0, bi = 0.0;
+    double be = 0.0, al = 0.0, br = 0.0, bi = 0.0, hm = 0.0;
     if (live) {
       const int64_t n = (int64_t)j * nlx + i;
       be = (double)betaG[n];
@@ -93,17 +94,23 @@ __device__ __forceinline__ void warp_body(const WarpSweepArgs& x, int l, float4 
       if (i == nlx - 1 && ifE) { br += a.wys[j] * lamL[2 * (1 * a.NE + j)]; bi += a.wys[j] * lamL[2 * (1 * a.NE + j) + 1]; }
       if (j == 0 && ifS) { br += a.wxs[i] * lamL[2 * (2 * a.NE + i)]; bi += a.wxs[i] * lamL[2 * (2 * a.NE + i) + 1]; }
       if (j == NY - 1 && ifN) { br += a.wxs[i] * lamL[2 * (3 * a.NE + i)]; bi += a.wxs[i] * lamL[2 * (3 * a.NE + i) + 1]; }
+      // interface boundary mass (k w on each interface edge of the node)
+      if (i == 0 && ifW) hm += a.wys[j] * kedgeL[0 * a.NE + j];
+      if (i == nlx - 1 && ifE) hm += a.wys[j] * kedgeL[1 * a.NE + j];
+      if (j == 0 && ifS) hm += a.wxs[i] * kedgeL[2 * a.NE + i];
+      if (j == NY - 1 && ifN) hm += a.wxs[i] * kedgeL[3 * a.NE + i];
     }
+    const float gm = (float)(-be * a.eta * hm);  // gamma = -beta w eta <c^-1 phi, phi>
     bet[j] = (float)(be * wx_lane * x.wyr[j]);  // beta' = beta Wx Wy
     const float fbr = (float)(be * br), fbi = (float)(be * bi);
     if (SRC) {
       bbr[j] = fbr;
       bbi[j] = fbi;
     }
-    if (j == 0) { al0 = (float)al; b0r = SRC ? 0.f : fbr; b0i = SRC ? 0.f : fbi; }
-    if (j == NY - 1) { alN = (float)al; bNr = SRC ? 0.f : fbr; bNi = SRC ? 0.f : fbi; }
+    if (j == 0) { al0 = (float)al; b0r = SRC ? 0.f : fbr; b0i = SRC ? 0.f : fbi; g0 = gm; }
+    if (j == NY - 1) { alN = (float)al; bNr = SRC ? 0.f : fbr; bNi = SRC ? 0.f : fbi; gN = gm; }
     if (j > 0 && j < NY - 1) {
-      if (slot < 2) ec[j][slot] = make_float4((float)(al - 1.0), SRC ? 0.f : fbr, SRC ? 0.f : fbi, 0.f);
+      if (slot < 2) ec[j][slot] = make_float4((float)(al - 1.0), SRC ? 0.f : fbr, SRC ? 0.f : fbi, gm);
     }
   }
   __syncwarp();
@@ -156,11 +163,11 @@ __device__ __forceinline__ void warp_body(const WarpSweepArgs& x, int l, float4 
         const float Ap = xr.apply(p[j], lane) + sy * Y;
         float f;
         if (j == 0) {
-          f = al0 * pd[j] - bet[j] * Ap + b0r * tb.x + b0i * tb.y;
+          f = al0 * pd[j] - bet[j] * Ap + b0r * tb.x + b0i * tb.y + g0 * p[j];
         } else if (j == NY - 1) {
-          f = alN * pd[j] - bet[j] * Ap + bNr * tb.x + bNi * tb.y;
+          f = alN * pd[j] - bet[j] * Ap + bNr * tb.x + bNi * tb.y + gN * p[j];
         } else {
-          f = edge_fix(pd[j] - bet[j] * Ap, pd[j], &ec[j][slot & 1], slot < 2, tb.x, tb.y);
+          f = edge_fix(pd[j] - bet[j] * Ap, pd[j], p[j], &ec[j][slot & 1], slot < 2, tb.x, tb.y);
         }
         if (SRC) f += bbr[j] * tb.x + bbi[j] * tb.y;
         pd[j] = f;
@@ -215,7 +222,6 @@ __device__ __forceinline__ void warp_body(const WarpSweepArgs& x, int l, float4 
     atomicAdd(a.wh_iter_sum, (unsigned long long)m_done);
   }
   const int NE = a.NE;
-  const double* kedgeL = a.kedge + (int64_t)l * 4 * NE;
   // S / N edges: lane i holds node (i, 0) and (i, NY-1)
   auto put = [&](int e, int t, bool has, double ur, double ui) {
     const bool iface = (e == 0) ? ifW : (e == 1) ? ifE : (e == 2) ? ifS : ifN;
@@ -226,8 +232,9 @@ __device__ __forceinline__ void warp_body(const WarpSweepArgs& x, int l, float4 
       if (t < len && has) {
         const double kk = kedgeL[e * NE + t];
         const double lr = lamL[2 * (e * NE + t)], li = lamL[2 * (e * NE + t) + 1];
-        dst[0] = -lr + 2.0 * kk * ui;
-        dst[1] = -li - 2.0 * kk * ur;
+        // -lambda + 2 k (eta - i zeta) u  (eta = 0, zeta = 1: -lambda - 2ik u)
+        dst[0] = -lr + 2.0 * kk * (a.eta * ur + a.zeta * ui);
+        dst[1] = -li + 2.0 * kk * (a.eta * ui - a.zeta * ur);
       } else {
         dst[0] = 0.0;
         dst[1] = 0.0;

@@ -129,13 +129,15 @@ struct XRowBand {
 
 // Edge-column correction of the p-dot update of a row.  The interior update
 // is f = p-dot - beta' A p; the two edge lanes add (alpha - 1) p-dot +
-// beta b_re cos + beta b_im sin with (alpha - 1, beta b_re, beta b_im) read
-// from shared memory.  Only the edge lanes load (no shared-memory traffic
-// for interior lanes) and no per-row default values are needed.
-__device__ __forceinline__ float edge_fix(float f, float pd, const float4* row, bool edge, float c, float s) {
+// beta b_re cos + beta b_im sin + gamma p with (alpha - 1, beta b_re,
+// beta b_im, gamma) read from shared memory (gamma = -beta x the interface
+// boundary mass of a generalised transmission condition, 0 by default).
+// Only the edge lanes load (no shared-memory traffic for interior lanes) and
+// no per-row default values are needed.
+__device__ __forceinline__ float edge_fix(float f, float pd, float p, const float4* row, bool edge, float c, float s) {
   if (edge) {
     const float4 e = *row;
-    f += e.x * pd + e.y * c + e.z * s;
+    f += e.x * pd + e.y * c + e.z * s + e.w * p;
   }
   return f;
 }

@@ -165,3 +165,24 @@ def test_packed_rejects_unsupported_shapes(hz):
         assert hz.hz_kernel_launches() == before
         torch.cuda.synchronize()
         case.close()
+
+
+def test_packed_sweep_with_generalised_transmission(hz):
+    """A member with the generalised interface condition (eta = 0.3,
+    zeta = 0.8) in a packed launch, against the oracle."""
+    from paper_2606_21695_gb300.api import Case
+
+    nx, ny, sx, sy, P, om = MEMBERS[2]
+    wl = configs.Workload("pkr", (0.0, 1.0, 0.0, 1.0), nx, ny, P, sx, sy, om, "random", (0.41, 0.57), 0.08,
+                          speed_seed=31, corr_len=0.3)
+    case = Case(wl, device=0)
+    hz.hz_problem_set(case.pr, hz.HZ_TRANSMISSION, np.array([0.3, 0.8]))
+    m = sem.Mesh(*wl.box, nx, ny, P, sx, sy)
+    gx, gy = m.coords_1d()
+    pr = dd.Problem(m, wl.speed(gx, gy), wl.omega, wl.source(gx, gy), wl.boundary(), robin=(0.3, 0.8))
+    nt = hz.hz_problem_nt(case.pr)
+    lam = _lam(pr, 77)
+    (gl, gu), = _packed(hz, [(case, pr, lam, nt)], 3, [True])
+    ref_l, ref_u, _ = pr.sweep(lam, pr.rhs(), nt, 3, want_u=True)
+    assert _rel(gu, ref_u) < 2e-4 and _rel(gl, ref_l) < 2e-4
+    case.close()

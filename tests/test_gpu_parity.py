@@ -32,10 +32,12 @@ def _wl(nx, ny, sx, sy, P, omega=9.0, kind="random", box=(0.0, 1.0, 0.0, 1.0)):
                             corr_len=0.3)
 
 
-def _pair(hz, wl, g_seed=None):
+def _pair(hz, wl, g_seed=None, robin=None):
     from paper_2606_21695_gb300.api import Case
 
     case = Case(wl, device=0)
+    if robin is not None:
+        hz.hz_problem_set(case.pr, hz.HZ_TRANSMISSION, np.array(robin, dtype=float))
     m = sem.Mesh(*wl.box, wl.nx, wl.ny, wl.P, wl.sub_nx, wl.sub_ny)
     gx, gy = m.coords_1d()
     g = wl.boundary()
@@ -45,7 +47,8 @@ def _pair(hz, wl, g_seed=None):
         from paper_2606_21695_gb300.api import boundary_vector
 
         hz.hz_problem_set(case.pr, hz.HZ_BOUNDARY, boundary_vector(g))
-    pr = dd.Problem(m, wl.speed(gx, gy), wl.omega, wl.source(gx, gy), g)
+    pr = dd.Problem(m, wl.speed(gx, gy), wl.omega, wl.source(gx, gy), g,
+                    robin=(0.0, 1.0) if robin is None else robin)
     # inputs agree (generators evaluated at each side's own coordinates)
     assert np.max(np.abs(case.c - pr.c)) < 1e-12
     return case, pr
@@ -132,6 +135,25 @@ def test_sweep_fp64_matches_oracle(hz, nx, ny, sx, sy, P):
     case.close()
 
 
+ROBIN_LAYOUTS = [(16, 16, 8, 8, 3), (8, 8, 4, 4, 2), (6, 4, 3, 2, 5), (8, 4, 2, 4, 1)]
+
+
+@pytest.mark.parametrize("nx,ny,sx,sy,P", ROBIN_LAYOUTS)
+def test_sweep_fp64_generalised_transmission_matches_oracle(hz, nx, ny, sx, sy, P):
+    """Interface condition d_n + k (eta - i zeta) (HZ_TRANSMISSION): zeta-scaled
+    interface damping in alpha / beta, the interface boundary mass in the
+    time stepping and the generalised update, FP64 against the oracle."""
+    robin = (0.3, 0.8)
+    wl = _wl(nx, ny, sx, sy, P)
+    case, pr = _pair(hz, wl, g_seed=nx + 2 * P, robin=robin)
+    nt = hz.hz_problem_nt(case.pr)
+    lam = _rand_lam(pr, 11)
+    got_l, got_u = _run_sweep(hz, case, pr, hz.HZ_FP64, nt, 2, lam, True)
+    ref_l, ref_u, _ = pr.sweep(lam, pr.rhs(), nt, 2, want_u=True)
+    assert _rel(got_u, ref_u) < 1e-12 and _rel(got_l, ref_l) < 1e-12
+    case.close()
+
+
 @pytest.fixture(params=["auto", "block", "warp2", "warp4"])
 def sweep_variant(request, monkeypatch):
     """auto: the register-resident kernel (one warp per subdomain) where
@@ -157,6 +179,44 @@ def test_sweep_fp32_within_bound(hz, sweep_variant, nx, ny, sx, sy, P):
         eu, el = _rel(got_u, ref_u), _rel(got_l, ref_l)
         print(f"fp32 sweep [{sweep_variant}] rhs={with_rhs} rel err u {eu:.2e} lambda {el:.2e} (Nt={nt})")
         assert eu < 2e-4 and el < 2e-4
+
+
+@pytest.mark.parametrize("variant,env,layout", [
+    ("warp", {"HZ_SWEEP_VARIANT": "warp"}, (16, 16, 8, 8, 3)),
+    ("band2", {"HZ_SWEEP_VARIANT": "warp", "HZ_SWEEP_WARPS": "2"}, (16, 16, 8, 8, 3)),
+    ("block", {"HZ_SWEEP_VARIANT": "block"}, (6, 4, 3, 2, 5)),
+    ("cluster", {"HZ_SWEEP_VARIANT": "cluster"}, (16, 16, 8, 8, 3)),
+    ("cband", {"HZ_SWEEP_VARIANT": "cband"}, (32, 16, 16, 16, 4)),
+])
+def test_sweep_fp32_generalised_transmission_all_kernels(hz, monkeypatch, variant, env, layout):
+    """Every FP32 sweep kernel with the generalised interface condition
+    (eta = 0.3, zeta = 0.8) against the oracle, with and without the source."""
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    nx, ny, sx, sy, P = layout
+    robin = (0.3, 0.8)
+    wl = _wl(nx, ny, sx, sy, P)
+    case, pr = _pair(hz, wl, g_seed=nx + P, robin=robin)
+    nt = hz.hz_problem_nt(case.pr)
+    lam = _rand_lam(pr, 12)
+    for with_rhs in (True, False):
+        got_l, got_u = _run_sweep(hz, case, pr, hz.HZ_FP32_REFINE, nt, 3, lam, with_rhs)
+        ref_l, ref_u, _ = pr.sweep(lam, pr.rhs() if with_rhs else None, nt, 3, want_u=True)
+        assert _rel(got_u, ref_u) < 2e-4 and _rel(got_l, ref_l) < 2e-4, variant
+    case.close()
+
+
+def test_solve_with_generalised_transmission_reaches_direct_solution(hz):
+    """FP32 sweeps + FP64 refinement with eta = 0.25: the solution is the
+    global discrete solution (the transmission condition changes only the
+    iteration count)."""
+    wl = _wl(16, 16, 4, 4, 3, omega=17.0)
+    case, pr = _pair(hz, wl, robin=(0.25, 1.0))
+    st, u, rep = hz.hz_solve(case.pr, hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=1e-10), n=case.n)
+    assert st == hz.HZ_OK and rep["rel_residual"] <= 1e-10
+    ud = pr.direct_solve().ravel()
+    assert np.max(np.abs(u - ud)) < 1e-7 * np.max(np.abs(ud))
+    case.close()
 
 
 def test_fp32_warp_variant_covers_benchmark_shape(hz, monkeypatch):

@@ -20,7 +20,7 @@ from oracle import dd, sem
 from workloads import fields
 
 
-def _problem(nx, ny, sx, sy, P, omega=6.0, seed=0, box=(0.0, 1.0, 0.0, 1.0), g=True, var_c=True):
+def _problem(nx, ny, sx, sy, P, omega=6.0, seed=0, box=(0.0, 1.0, 0.0, 1.0), g=True, var_c=True, robin=(0.0, 1.0)):
     m = sem.Mesh(*box, nx, ny, P, sx, sy)
     X, Y = m.coords()
     rng = np.random.default_rng(seed)
@@ -30,7 +30,7 @@ def _problem(nx, ny, sx, sy, P, omega=6.0, seed=0, box=(0.0, 1.0, 0.0, 1.0), g=T
     if g:
         gg = {k: rng.standard_normal(n) + 1j * rng.standard_normal(n)
               for k, n in (("S", m.NX), ("N", m.NX), ("W", m.NY), ("E", m.NY))}
-    return dd.Problem(m, c, omega, f, gg)
+    return dd.Problem(m, c, omega, f, gg, robin=robin)
 
 
 @pytest.mark.parametrize("P,Nt", [(1, 7), (2, 12), (3, 40), (4, 25)])
@@ -91,6 +91,25 @@ def test_waveholtz_converges_to_dense_subdomain_solve():
     assert np.max(np.abs(u5 - exact)) / np.max(np.abs(exact)) > err
 
 
+@pytest.mark.parametrize("robin", [(0.4, 0.7), (1.0, 1.5)])
+def test_waveholtz_with_interface_boundary_mass_converges_to_dense_solve(robin):
+    """Generalised interface condition d_n + k (eta - i zeta): the subdomain
+    operator gains zeta-scaled damping and a boundary mass on interface
+    edges; WaveHoltz with the boundary mass in the time stepping converges
+    to the dense solve of that operator, and Pi(u*) = u* holds exactly."""
+    pr = _problem(4, 4, 2, 2, 2, omega=4.0, seed=4, robin=robin)
+    m = pr.mesh
+    assert np.max(pr.Hm_sub) > 0
+    rng = np.random.default_rng(5)
+    b = rng.standard_normal((m.L, m.nly, m.nlx)) + 1j * rng.standard_normal((m.L, m.nly, m.nlx))
+    exact = np.stack([np.linalg.solve(pr.sub_matrix(l).toarray(), b[l].ravel()).reshape(b[l].shape)
+                      for l in range(m.L)])
+    u, _ = pr.waveholtz(b, pr.choose_nt(), 120)
+    assert np.max(np.abs(u - exact)) / np.max(np.abs(exact)) < 1e-9
+    u1, _ = pr.waveholtz(b, pr.choose_nt(), 1, u0=exact)
+    assert np.max(np.abs(u1 - exact)) < 1e-11 * np.max(np.abs(exact))
+
+
 LAYOUTS = [
     (4, 4, 2, 2, 2),  # 2x2 subdomains, one cross point
     (6, 6, 2, 2, 1),  # 3x3, four cross points, P = 1
@@ -119,6 +138,50 @@ def test_dd_fixed_point_equals_global_direct_solve(nx, ny, sx, sy, P):
             rows, cols, _ = pr.edge_nodes(e)
             rr, rc, _ = pr.edge_nodes(dd.OPPOSITE[e])
             assert np.max(np.abs(us[l, rows, cols] - us[r, rr, rc])) < 1e-9 * np.max(np.abs(ud))
+
+
+@pytest.mark.parametrize("robin", [(0.3, 0.8), (0.5, 1.3)])
+@pytest.mark.parametrize("nx,ny,sx,sy,P", [(4, 4, 2, 2, 2), (6, 6, 2, 2, 1), (4, 6, 2, 3, 4)])
+def test_dd_fixed_point_with_generalised_transmission_condition(nx, ny, sx, sy, P, robin):
+    """Interface condition d_n + k (eta - i zeta) with update
+    lambda_r = -lambda_l + 2k(eta - i zeta) u: the DD fixed point is still the
+    global discrete solution (cross points included), the iteration count is
+    what changes."""
+    pr = _problem(nx, ny, sx, sy, P, omega=7.0, seed=nx + P, robin=robin)
+    ud = pr.direct_solve()
+    u, info = pr.dd_solve(pr.rhs(), outer="gmres", restart=200, tol=1e-13, max_sweeps=400, inner="direct")
+    assert np.linalg.norm(u - ud) / np.linalg.norm(ud) < 1e-10, info["sweeps"]
+
+
+def test_generalised_condition_negative_control():
+    """Plant a wrong update (the eta term with the opposite sign): the DD
+    fixed point is no longer the global solution."""
+    pr = _problem(4, 4, 2, 2, 2, omega=7.0, seed=6, robin=(0.5, 1.0))
+    ud = pr.direct_solve()
+    orig = dd.Problem.sweep
+
+    def wrong(self, lam_in, *a, **k):
+        k2 = dict(k)
+        k2["want_u"] = True
+        lam_out, u, it = orig(self, lam_in, *a, **k2)
+        w = self.omega
+        for e in range(4):
+            rows, cols, _ = self.edge_nodes(e)
+            n = len(rows)
+            for l in np.where(self.nbr[:, e] >= 0)[0]:
+                r = self.nbr[l, e]
+                kk = w / self.c_sub[l, rows, cols]
+                lam_out[r, dd.OPPOSITE[e], :n] -= 4 * kk * self.eta * u[l, rows, cols]
+        return (lam_out, u, it) if k.get("want_u", False) else lam_out
+
+    u_ok, _ = pr.dd_solve(pr.rhs(), restart=200, tol=1e-13, max_sweeps=400, inner="direct")
+    assert np.linalg.norm(u_ok - ud) / np.linalg.norm(ud) < 1e-10
+    dd.Problem.sweep = wrong
+    try:
+        u_bad, _ = pr.dd_solve(pr.rhs(), restart=200, tol=1e-13, max_sweeps=400, inner="direct")
+    finally:
+        dd.Problem.sweep = orig
+    assert np.linalg.norm(u_bad - ud) / np.linalg.norm(ud) > 1e-3
 
 
 def test_dd_paper_sign_does_not_give_global_solution(monkeypatch):
