@@ -56,6 +56,7 @@ def parse():
                     help="sweep: only run --sweeps DD sweeps of the workload (for ncu captures); "
                          "batch: batched solves of the multi-problem workload; serve: served request stream")
     ap.add_argument("--batch", type=int, default=12, help="problems in --mode batch")
+    ap.add_argument("--small-batch", type=int, default=32, help="small problems in --mode batch")
     ap.add_argument("--requests", type=int, default=40, help="arrivals in --mode serve")
     ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals per second in --mode serve")
     ap.add_argument("--baseline-requests", type=int, default=12)
@@ -527,6 +528,18 @@ def run_batch(args):
     res["packable_problems"] = [w.name for w in pw]
     res["cheapest_packable"] = _batch_group(hz, pcases, 5000)
     for c in pcases:
+        c.close()
+    # many small problems of the batched workload's smallest shape (64^2 quads, P = 2,
+    # 4x4-element subdomains), frequencies and sources varied: the launch-bound regime
+    from workloads import configs
+
+    small = [configs.Workload(f"small{k:02d}", (0.0, 1.0, 0.0, 1.0), 64, 64, 2, 4, 4, 8.0 + 0.5 * k, "random",
+                              (0.3 + 0.01 * k, 0.6 - 0.01 * k), 0.03, speed_seed=100 + k, corr_len=0.1)
+             for k in range(args.small_batch)]
+    scases = [Case(w) for w in small]
+    res["small_problems"] = f"{len(small)} x (64x64 quads, P=2, 16x16 subdomains of 4x4)"
+    res["small"] = _batch_group(hz, scases, 5000)
+    for c in scases:
         c.close()
     return res
 

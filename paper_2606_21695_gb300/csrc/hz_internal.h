@@ -99,6 +99,7 @@ constexpr int kWarpMaxRows = 33;
 struct WarpSweepArgs {
   SweepArgs base;
   int L;
+  int shape;                                   // packed launches: shape id (packed_shape_id)
   float sy;                                    // 4 / hy^2
   float wyr[kWarpMaxRows];                     // hy/2 * (w_a [own element] + w_P [element below])
 };
@@ -108,11 +109,12 @@ struct WarpSweepArgs {
 hz_status launch_sweep_warp(int P, int sy, int h, const WarpSweepArgs& a, cudaStream_t st);
 
 // Packed sweep of several problems in one launch (register-resident body, one
-// warp per subdomain).  descs: per-problem parameters in device memory;
-// items: {descriptor index, subdomain, shape id, 1 if a source is swept}.
+// warp per subdomain).  descs: R per-problem parameter sets in device memory
+// (shape ids in descs[d].shape); offsets: R+1 running subdomain counts in
+// device memory (item it belongs to the d with offsets[d] <= it < offsets[d+1]).
 // packed_shape_id returns -1 when (P, sub_ny, nlx) has no packed variant.
 int packed_shape_id(int P, int sny, int nlx);
-hz_status launch_sweep_packed(const WarpSweepArgs* descs, const int4* items, int nitems, cudaStream_t st);
+hz_status launch_sweep_packed(const WarpSweepArgs* descs, const int* offsets, int R, cudaStream_t st);
 
 // FP32 sweep of one subdomain per thread-block cluster (column bands, halo
 // exchange through distributed shared memory).  HZ_ERR_UNSUPPORTED when no

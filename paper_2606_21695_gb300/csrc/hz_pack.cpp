@@ -63,6 +63,9 @@ hz_status Packer::submit(Problem& pr, const WarpSweepArgs& x, int shape, cudaStr
   Req r{&pr, x, shape, x.base.rhs != nullptr, st};
   std::unique_lock<std::mutex> lk(mu_);
   pending_.push_back(&r);
+  // Launch when every member has a request pending, or when the oldest
+  // request has waited wait_us.  (Launching as soon as the previous packed
+  // launch had finished was measured slower: smaller packs, more launches.)
   if ((int)pending_.size() >= members_) {
     launch_locked();
   } else {
@@ -107,48 +110,30 @@ hz_status Packer::launch_batch(std::vector<Req*>& batch) {
     return a->pr < b->pr;
   });
   const int R = (int)batch.size();
-  std::vector<long long> key;
-  key.reserve(3 * R);
-  int nitems = 0;
-  for (const Req* r : batch) {
-    key.push_back((long long)(uintptr_t)r->pr);
-    key.push_back(((long long)r->shape << 1) | (r->src ? 1 : 0));
-    key.push_back(((long long)r->x.L << 32) | (long long)(r->x.base.Nt * 1024 + r->x.base.m_wh));
-    nitems += r->x.L;
-  }
-  if (key != plan_key_) {
-    // new set of problems: rebuild the item list (after the previous launch
-    // that reads the old one has been issued, its host staging may be reused
-    // only when the copy is done)
-    HZ_CUDA(cudaStreamSynchronize(st_));
-    HZ_TRY(hitems_.ensure((size_t)nitems * sizeof(int4)));
-    HZ_TRY(ditems_.ensure((size_t)nitems * sizeof(int4)));
-    int4* it = hitems_.as<int4>();
-    int k = 0;
-    for (int d = 0; d < R; ++d) {
-      const Req* r = batch[d];
-      for (int l = 0; l < r->x.L; ++l) it[k++] = make_int4(d, l, r->shape, r->src ? 1 : 0);
-    }
-    HZ_CUDA(cudaMemcpyAsync(ditems_.ptr, hitems_.ptr, (size_t)nitems * sizeof(int4), cudaMemcpyHostToDevice, st_));
-    plan_key_ = key;
-    nitems_ = nitems;
-  }
-  // descriptors into the next ring slot
+  // descriptors, then R + 1 running subdomain counts, into the next ring slot
   const int slot = ring_;
   ring_ = (ring_ + 1) % kRing;
   HZ_CUDA(cudaEventSynchronize(ring_ev_[slot]));  // its previous copy is done
   const size_t db = (size_t)R * sizeof(WarpSweepArgs);
-  if (db > ddesc_[slot].bytes) {
+  const size_t total = db + (size_t)(R + 1) * sizeof(int);
+  if (total > ddesc_[slot].bytes) {
     HZ_CUDA(cudaStreamSynchronize(st_));
-    HZ_TRY(ddesc_[slot].ensure(db));
+    HZ_TRY(ddesc_[slot].ensure(total));
   }
-  HZ_TRY(hdesc_[slot].ensure(db));
+  HZ_TRY(hdesc_[slot].ensure(total));
   WarpSweepArgs* hd = hdesc_[slot].as<WarpSweepArgs>();
-  for (int d = 0; d < R; ++d) hd[d] = batch[d]->x;
+  int* off = reinterpret_cast<int*>(static_cast<char*>(hdesc_[slot].ptr) + db);
+  off[0] = 0;
+  for (int d = 0; d < R; ++d) {
+    hd[d] = batch[d]->x;
+    hd[d].shape = batch[d]->shape;
+    off[d + 1] = off[d] + batch[d]->x.L;
+  }
   for (const Req* r : batch) HZ_CUDA(cudaStreamWaitEvent(st_, r->pr->pack_ready, 0));
-  HZ_CUDA(cudaMemcpyAsync(ddesc_[slot].ptr, hd, db, cudaMemcpyHostToDevice, st_));
+  HZ_CUDA(cudaMemcpyAsync(ddesc_[slot].ptr, hdesc_[slot].ptr, total, cudaMemcpyHostToDevice, st_));
   HZ_CUDA(cudaEventRecord(ring_ev_[slot], st_));
-  HZ_TRY(launch_sweep_packed(ddesc_[slot].as<WarpSweepArgs>(), ditems_.as<int4>(), nitems_, st_));
+  HZ_TRY(launch_sweep_packed(ddesc_[slot].as<WarpSweepArgs>(),
+                             reinterpret_cast<const int*>(static_cast<const char*>(ddesc_[slot].ptr) + db), R, st_));
   ++launches_;
   HZ_CUDA(cudaEventRecord(done_, st_));
   for (const Req* r : batch) HZ_CUDA(cudaStreamWaitEvent(r->st, done_, 0));

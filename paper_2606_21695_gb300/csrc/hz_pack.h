@@ -60,18 +60,12 @@ class Packer {
   long wait_us_;
   cudaStream_t st_ = nullptr;
   cudaEvent_t done_ = nullptr;
-  // descriptor ring (pinned host staging -> device), one event per slot
+  // descriptor + running-count ring (pinned host staging -> device), one event per slot
   static constexpr int kRing = 4;
   HostBuf hdesc_[kRing];
   DevBuf ddesc_[kRing];
   cudaEvent_t ring_ev_[kRing] = {};
   int ring_ = 0;
-  // work items of the last plan (kept on the device while the same set of
-  // problems and shapes repeats)
-  std::vector<long long> plan_key_;
-  HostBuf hitems_;
-  DevBuf ditems_;
-  int nitems_ = 0;
   uint64_t launches_ = 0;
 };
 

@@ -1211,7 +1211,7 @@ hz_status hz_sweep_packed(const hz_problem* problems, int32_t count, const int32
     int dev = 0;
     HZ_CUDA(cudaGetDevice(&dev));
     std::vector<WarpSweepArgs> descs(count);
-    std::vector<int4> items;
+    std::vector<int> offsets(count + 1, 0);
     for (int k = 0; k < count; ++k) {
       if (!problems[k] || !lam_in[k] || !lam_out[k]) return fail(HZ_ERR_INVALID_ARG, "null problem or buffer");
       if (lam_in[k] == lam_out[k]) return fail(HZ_ERR_INVALID_ARG, "lam_in and lam_out must not alias");
@@ -1227,15 +1227,16 @@ hz_status hz_sweep_packed(const hz_problem* problems, int32_t count, const int32
       double* uk = u_sub ? u_sub[k] : nullptr;
       descs[k].base = make_sweep_args(pr, true, nts[k], wh_iters, 0.0, lam_in[k], lam_out[k], rk, uk);
       descs[k].L = g.L;
+      descs[k].shape = shape;
       warp_rows(g, &descs[k]);
-      for (int l = 0; l < g.L; ++l) items.push_back(make_int4(k, l, shape, rk ? 1 : 0));
+      offsets[k + 1] = offsets[k] + g.L;
     }
     DevBuf dd, di;
     HZ_TRY(dd.ensure(descs.size() * sizeof(WarpSweepArgs)));
-    HZ_TRY(di.ensure(items.size() * sizeof(int4)));
+    HZ_TRY(di.ensure(offsets.size() * sizeof(int)));
     HZ_CUDA(cudaMemcpyAsync(dd.ptr, descs.data(), descs.size() * sizeof(WarpSweepArgs), cudaMemcpyHostToDevice, st));
-    HZ_CUDA(cudaMemcpyAsync(di.ptr, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
-    HZ_TRY(launch_sweep_packed(dd.as<WarpSweepArgs>(), di.as<int4>(), (int)items.size(), st));
+    HZ_CUDA(cudaMemcpyAsync(di.ptr, offsets.data(), offsets.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    HZ_TRY(launch_sweep_packed(dd.as<WarpSweepArgs>(), di.as<int>(), count, st));
     HZ_CUDA(cudaStreamSynchronize(st));  // the tables are freed on return
     for (int k = 0; k < count; ++k) problems[k]->last_variant = kVariantPacked;
     return HZ_OK;

@@ -3,12 +3,14 @@
 // frequencies and N_t), every subdomain of every problem swept by one warp
 // with the register-resident body of hz_sweep_warp.cuh.
 //
-// The launch is persistent: a grid of at most (resident blocks per SM) x
-// (SMs) one-warp blocks walks a list of work items {problem, subdomain,
-// shape}, sorted by decreasing cost (subdomain nodes x (N_t - 1) x WaveHoltz
-// iterations) so the longest items start first.  Per-problem parameters are
-// read from a table in global memory; the y-stiffness coefficients are the
-// compile-time tables every problem of a degree shares.
+// The launch is persistent: a grid of (resident blocks per SM) x (SMs)
+// one-warp blocks walks the items (problem, subdomain) of all problems, the
+// problems in decreasing order of cost per subdomain (nodes x (N_t - 1) x
+// WaveHoltz iterations), so the longest items start first; an item finds its
+// problem by binary search in the running subdomain counts.  Per-problem
+// parameters (with the compiled shape id) are read from a table in global
+// memory; the y-stiffness coefficients are the compile-time tables every
+// problem of a degree shares.
 #include <cuda_runtime.h>
 
 #include "hz_sweep_warp.cuh"
@@ -33,18 +35,26 @@ namespace {
 constexpr int kPackedMaxRows = 25;
 
 __global__ void __launch_bounds__(32) sweep_packed_kernel(const WarpSweepArgs* __restrict__ descs,
-                                                           const int4* __restrict__ items, int nitems) {
+                                                           const int* __restrict__ offsets, int R) {
   __shared__ float4 ec[kPackedMaxRows][2];
+  const int nitems = offsets[R];
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const int4 w = items[it];  // {descriptor, subdomain, shape, with source}
-    const WarpSweepArgs& x = descs[w.x];
-    switch (2 * w.z + w.w) {
+    // the problem holding item it: offsets[d] <= it < offsets[d + 1]
+    int lo = 0, hi = R - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (offsets[mid] <= it) lo = mid;
+      else hi = mid - 1;
+    }
+    const WarpSweepArgs& x = descs[lo];
+    const int l = it - offsets[lo];
+    switch (2 * x.shape + (x.base.rhs != nullptr ? 1 : 0)) {
 #define HZ_CASE(ID, P, SY)                                                 \
-  case 2 * ID: warp_sweep::warp_body<P, SY, false, false>(x, w.y, ec, nullptr); break; \
-  case 2 * ID + 1: warp_sweep::warp_body<P, SY, true, false>(x, w.y, ec, nullptr); break;
+  case 2 * ID: warp_sweep::warp_body<P, SY, false, false>(x, l, ec, nullptr); break; \
+  case 2 * ID + 1: warp_sweep::warp_body<P, SY, true, false>(x, l, ec, nullptr); break;
       HZ_PACKED_SHAPES(HZ_CASE)
 #undef HZ_CASE
-      default: break;  // the host only builds items for compiled shapes
+      default: break;  // the host only packs compiled shapes
     }
     __syncwarp();  // the edge table is rewritten by the next item
   }
@@ -61,15 +71,14 @@ int packed_shape_id(int P, int sny, int nlx) {
   return -1;
 }
 
-hz_status launch_sweep_packed(const WarpSweepArgs* descs, const int4* items, int nitems, cudaStream_t st) {
-  if (nitems <= 0) return HZ_OK;
+hz_status launch_sweep_packed(const WarpSweepArgs* descs, const int* offsets, int R, cudaStream_t st) {
+  if (R <= 0) return HZ_OK;
   int dev = 0, sms = 0, per_sm = 0;
   HZ_CUDA(cudaGetDevice(&dev));
   HZ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   HZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_packed_kernel, 32, 0));
   if (per_sm < 1) per_sm = 1;
-  const int grid = nitems < per_sm * sms ? nitems : per_sm * sms;
-  sweep_packed_kernel<<<grid, 32, 0, st>>>(descs, items, nitems);
+  sweep_packed_kernel<<<per_sm * sms, 32, 0, st>>>(descs, offsets, R);
   note_launch();
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
