@@ -37,7 +37,9 @@ __host__ __device__ constexpr bool tap(int P, int ne, int j, int t) {
 // ec: per-warp shared table of the edge columns' rows; uo: per-warp shared
 // stash of the previous iterate, used only when STASH and a WaveHoltz
 // tolerance is set (may be null otherwise).
-template <int P, int SY, bool SRC, bool STASH>
+// RM: the interface boundary mass of a generalised transmission condition may
+// be non-zero (eta != 0); without it the two terms it adds are compiled out.
+template <int P, int SY, bool SRC, bool STASH, bool RM = true>
 __device__ __forceinline__ void warp_body(const WarpSweepArgs& x, int l, float4 (*ec)[2], float2* uo) {
   constexpr int NY = SY * P + 1;
   constexpr int NB = SRC ? NY : 1;  // per-node forcing only when a source is present
@@ -163,11 +165,13 @@ __device__ __forceinline__ void warp_body(const WarpSweepArgs& x, int l, float4 
         const float Ap = xr.apply(p[j], lane) + sy * Y;
         float f;
         if (j == 0) {
-          f = al0 * pd[j] - bet[j] * Ap + b0r * tb.x + b0i * tb.y + g0 * p[j];
+          f = al0 * pd[j] - bet[j] * Ap + b0r * tb.x + b0i * tb.y;
+          if (RM) f += g0 * p[j];
         } else if (j == NY - 1) {
-          f = alN * pd[j] - bet[j] * Ap + bNr * tb.x + bNi * tb.y + gN * p[j];
+          f = alN * pd[j] - bet[j] * Ap + bNr * tb.x + bNi * tb.y;
+          if (RM) f += gN * p[j];
         } else {
-          f = edge_fix(pd[j] - bet[j] * Ap, pd[j], p[j], &ec[j][slot & 1], slot < 2, tb.x, tb.y);
+          f = edge_fix<RM>(pd[j] - bet[j] * Ap, pd[j], p[j], &ec[j][slot & 1], slot < 2, tb.x, tb.y);
         }
         if (SRC) f += bbr[j] * tb.x + bbi[j] * tb.y;
         pd[j] = f;
@@ -270,14 +274,14 @@ __device__ __forceinline__ void warp_body(const WarpSweepArgs& x, int l, float4 
 
 // One subdomain (one warp) per block: 1024 subdomains spread as 6-7 blocks
 // per SM over 152 SMs, instead of multi-warp blocks landing unevenly.
-template <int P, int SY, bool SRC>
+template <int P, int SY, bool SRC, bool RM>
 __global__ void __launch_bounds__(32) sweep_warp_kernel(const __grid_constant__ WarpSweepArgs x) {
   constexpr int NY = SY * P + 1;
   __shared__ float4 ec[NY][2];
   __shared__ float2 uo[NY * 32];
   const int l = blockIdx.x;
   if (l >= x.L) return;
-  warp_body<P, SY, SRC, true>(x, l, ec, uo);
+  warp_body<P, SY, SRC, true, RM>(x, l, ec, uo);
 }
 
 }  // namespace warp_sweep

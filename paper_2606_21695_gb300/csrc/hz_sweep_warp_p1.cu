@@ -11,8 +11,14 @@ template <int P, int SY, int H>
 hz_status launch(const WarpSweepArgs& a, cudaStream_t st) {
   if constexpr (H == 1) {
     const int blocks = a.L;  // one subdomain (one warp) per block
-    if (a.base.rhs) sweep_warp_kernel<P, SY, true><<<blocks, 32, 0, st>>>(a);
-    else sweep_warp_kernel<P, SY, false><<<blocks, 32, 0, st>>>(a);
+    const bool rm = a.base.eta != 0.0;  // interface boundary mass present
+    if (a.base.rhs) {
+      if (rm) sweep_warp_kernel<P, SY, true, true><<<blocks, 32, 0, st>>>(a);
+      else sweep_warp_kernel<P, SY, true, false><<<blocks, 32, 0, st>>>(a);
+    } else {
+      if (rm) sweep_warp_kernel<P, SY, false, true><<<blocks, 32, 0, st>>>(a);
+      else sweep_warp_kernel<P, SY, false, false><<<blocks, 32, 0, st>>>(a);
+    }
   } else {
     const int blocks = a.L;  // one subdomain (H warps) per block
     if (a.base.rhs) band_sweep::sweep_band_kernel<P, SY, true, H><<<blocks, H * 32, 0, st>>>(a);

@@ -134,10 +134,12 @@ struct XRowBand {
 // boundary mass of a generalised transmission condition, 0 by default).
 // Only the edge lanes load (no shared-memory traffic for interior lanes) and
 // no per-row default values are needed.
+template <bool RM = true>
 __device__ __forceinline__ float edge_fix(float f, float pd, float p, const float4* row, bool edge, float c, float s) {
   if (edge) {
     const float4 e = *row;
-    f += e.x * pd + e.y * c + e.z * s + e.w * p;
+    f += e.x * pd + e.y * c + e.z * s;
+    if (RM) f += e.w * p;  // RM = false: the boundary mass is known to be zero
   }
   return f;
 }
