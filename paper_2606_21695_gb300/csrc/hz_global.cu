@@ -237,57 +237,132 @@ __global__ void assemble_add_kernel(const __grid_constant__ AssembleArgs a, cons
 }
 
 // ---- Krylov vector kernels (vectors of n2 doubles = n2/2 complex values)
-// One block per contiguous chunk of the vectors: the chunk of w is staged in
-// shared memory once, then the block's warps take the basis vectors in turn
-// (coalesced reads of each V_k chunk, warp reduction), so every element of V
-// and w is read from memory once per call.  part[(blk * nv + k) * 2 + {0, 1}].
+// On this part FP64 arithmetic, not memory, bounds these kernels (the FP64
+// pipe retires about 1/65 of the FP32 rate), so they are written for the
+// fewest FP64 instructions: every complex multiply-accumulate is four fma()
+// (no separate multiply and add), the real variants skip the imaginary half,
+// and the difference w = v - S v and the final norm ride along with the dot
+// and update passes instead of running as passes of their own.
+//
+// multi_dot: one block per contiguous chunk of the vectors: the chunk of w is
+// staged in shared memory once, then the block's warps take the basis vectors
+// in turn (coalesced reads of each V_k chunk, two accumulator pairs per lane,
+// one warp reduction per vector), so every element of V and w is read from
+// memory once per call.  part[(blk * nv + k) * 2 + {0, 1}].
 constexpr int kDotWarps = 8;
+template <bool REAL, bool DIFF>
 __global__ void __launch_bounds__(kDotWarps * 32)
-    multi_dot_kernel(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ w, int64_t nc,
-                     int chunk, int real_dot, double* __restrict__ part) {
+    multi_dot_kernel(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ w,
+                     const double* __restrict__ w_sub, double* __restrict__ w_out, int64_t nc, int chunk,
+                     double* __restrict__ part) {
   extern __shared__ double2 ws[];
   const int64_t r0 = (int64_t)blockIdx.x * chunk;
   const int rows = (int)((nc - r0) < chunk ? (nc - r0) : chunk);
-  const double2* w2 = reinterpret_cast<const double2*>(w);
-  for (int q = threadIdx.x; q < rows; q += blockDim.x) ws[q] = w2[r0 + q];
+  for (int q = threadIdx.x; q < rows; q += blockDim.x) {
+    double2 x = reinterpret_cast<const double2*>(w)[r0 + q];
+    if (DIFF) {
+      const double2 y = reinterpret_cast<const double2*>(w_sub)[r0 + q];
+      x.x -= y.x;
+      x.y -= y.y;
+      reinterpret_cast<double2*>(w_out)[r0 + q] = x;
+    }
+    ws[q] = x;
+  }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = warp; k < nv; k += kDotWarps) {
     const double2* vk = reinterpret_cast<const double2*>(V + (int64_t)k * ld) + r0;
-    double sr = 0.0, si = 0.0;
-#pragma unroll 4
-    for (int q = lane; q < rows; q += 32) {
-      const double2 a = vk[q], b = ws[q];
-      sr += a.x * b.x + a.y * b.y;  // Re conj(a) b
-      si += a.x * b.y - a.y * b.x;  // Im conj(a) b
+    // conj(a) b = (a.x b.x + a.y b.y) + i (a.x b.y - a.y b.x)
+    double sr0 = 0.0, si0 = 0.0, sr1 = 0.0, si1 = 0.0;
+    int q = lane;
+#pragma unroll 2
+    for (; q + 32 < rows; q += 64) {
+      const double2 a = vk[q], b = ws[q], c = vk[q + 32], d = ws[q + 32];
+      sr0 = fma(a.x, b.x, sr0);
+      sr0 = fma(a.y, b.y, sr0);
+      sr1 = fma(c.x, d.x, sr1);
+      sr1 = fma(c.y, d.y, sr1);
+      if (!REAL) {
+        si0 = fma(a.x, b.y, si0);
+        si0 = fma(-a.y, b.x, si0);
+        si1 = fma(c.x, d.y, si1);
+        si1 = fma(-c.y, d.x, si1);
+      }
     }
-    sr = warp_sum(sr);
-    si = warp_sum(si);
+    if (q < rows) {
+      const double2 a = vk[q], b = ws[q];
+      sr0 = fma(a.x, b.x, sr0);
+      sr0 = fma(a.y, b.y, sr0);
+      if (!REAL) {
+        si0 = fma(a.x, b.y, si0);
+        si0 = fma(-a.y, b.x, si0);
+      }
+    }
+    const double sr = warp_sum(sr0 + sr1);
+    const double si = REAL ? 0.0 : warp_sum(si0 + si1);
     if (lane == 0) {
       double* p = part + ((int64_t)blockIdx.x * nv + k) * 2;
       p[0] = sr;
-      p[1] = real_dot ? 0.0 : si;
+      p[1] = si;
     }
   }
 }
 
+// w -= sum_k h_k V_k, one complex entry per thread and iteration, basis
+// vectors taken two at a time into separate accumulators; NORM: the block's
+// partial ||w_new||^2 into norm_part[2 blk] (0 into norm_part[2 blk + 1]).
+template <bool REAL, bool NORM>
 __global__ void multi_axpy_kernel(const double* __restrict__ V, int64_t ld, int nv, const double* __restrict__ h,
-                                  double* __restrict__ w, int64_t n2, int real_coef) {
+                                  double* __restrict__ w, int64_t nc, double* __restrict__ norm_part) {
   extern __shared__ double hs[];
   for (int k = threadIdx.x; k < 2 * nv; k += blockDim.x) hs[k] = h[k];
   __syncthreads();
-  const int64_t nc = n2 / 2;
   double2* w2 = reinterpret_cast<double2*>(w);
+  double nrm[1] = {0.0};
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += (int64_t)gridDim.x * blockDim.x) {
-    double2 acc = w2[q];
-#pragma unroll 4
-    for (int k = 0; k < nv; ++k) {
+    // (hr + i hi)(v.x + i v.y) = (hr v.x - hi v.y) + i (hr v.y + hi v.x)
+    double2 acc = w2[q], acc1 = make_double2(0.0, 0.0);
+    int k = 0;
+#pragma unroll 2
+    for (; k + 1 < nv; k += 2) {
       const double2 v = reinterpret_cast<const double2*>(V + (int64_t)k * ld)[q];
-      const double hr = hs[2 * k], hi = real_coef ? 0.0 : hs[2 * k + 1];
-      acc.x -= hr * v.x - hi * v.y;
-      acc.y -= hr * v.y + hi * v.x;
+      const double2 u = reinterpret_cast<const double2*>(V + (int64_t)(k + 1) * ld)[q];
+      const double hr = hs[2 * k], hr1 = hs[2 * k + 2];
+      acc.x = fma(-hr, v.x, acc.x);
+      acc.y = fma(-hr, v.y, acc.y);
+      acc1.x = fma(-hr1, u.x, acc1.x);
+      acc1.y = fma(-hr1, u.y, acc1.y);
+      if (!REAL) {
+        const double hi = hs[2 * k + 1], hi1 = hs[2 * k + 3];
+        acc.x = fma(hi, v.y, acc.x);
+        acc.y = fma(-hi, v.x, acc.y);
+        acc1.x = fma(hi1, u.y, acc1.x);
+        acc1.y = fma(-hi1, u.x, acc1.y);
+      }
     }
+    if (k < nv) {
+      const double2 v = reinterpret_cast<const double2*>(V + (int64_t)k * ld)[q];
+      const double hr = hs[2 * k];
+      acc.x = fma(-hr, v.x, acc.x);
+      acc.y = fma(-hr, v.y, acc.y);
+      if (!REAL) {
+        const double hi = hs[2 * k + 1];
+        acc.x = fma(hi, v.y, acc.x);
+        acc.y = fma(-hi, v.x, acc.y);
+      }
+    }
+    acc.x += acc1.x;
+    acc.y += acc1.y;
     w2[q] = acc;
+    if (NORM) nrm[0] = fma(acc.x, acc.x, fma(acc.y, acc.y, nrm[0]));
+  }
+  if (NORM) {
+    __shared__ double res[1];
+    block_sum<1>(nrm, res);
+    if (threadIdx.x == 0) {
+      norm_part[2 * blockIdx.x] = res[0];
+      norm_part[2 * blockIdx.x + 1] = 0.0;
+    }
   }
 }
 
@@ -375,32 +450,57 @@ hz_status launch_assemble_add(const AssembleArgs& a, const double* u_sub, double
   return HZ_OK;
 }
 
-// blocks for multi_dot: ~2 per SM, chunks of at most 4096 complex entries (64 KB of shared memory)
+// blocks for multi_dot: 2 per SM, chunks of at most 4096 complex entries (64 KB of shared memory)
 int vec_blocks(int64_t n2) {
   const int64_t nc = n2 / 2;
-  int64_t nb = 304;
+  int64_t nb = 2 * 152;
   if ((nc + nb - 1) / nb > 4096) nb = (nc + 4095) / 4096;
   if (nb > nc) nb = nc > 0 ? nc : 1;
   return (int)nb;
 }
 
-hz_status launch_multi_dot(const double* V, int64_t ld, int nv, const double* w, int64_t n2, bool real_dot,
-                           double* part, int nblocks, cudaStream_t st) {
-  const int64_t nc = n2 / 2;
-  const int chunk = (int)((nc + nblocks - 1) / nblocks);
-  const size_t smem = (size_t)chunk * sizeof(double2);
+template <bool REAL, bool DIFF>
+hz_status launch_multi_dot_T(const double* V, int64_t ld, int nv, const double* w, const double* w_sub, double* w_out,
+                             int64_t nc, int chunk, size_t smem, double* part, int nblocks, cudaStream_t st) {
   if (smem > 48 * 1024)
-    HZ_CUDA(cudaFuncSetAttribute(multi_dot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  multi_dot_kernel<<<nblocks, kDotWarps * 32, smem, st>>>(V, ld, nv, w, nc, chunk, real_dot ? 1 : 0, part);
+    HZ_CUDA(cudaFuncSetAttribute(multi_dot_kernel<REAL, DIFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  multi_dot_kernel<REAL, DIFF><<<nblocks, kDotWarps * 32, smem, st>>>(V, ld, nv, w, w_sub, w_out, nc, chunk, part);
   note_launch();
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;
 }
 
+hz_status launch_multi_dot(const double* V, int64_t ld, int nv, const double* w, const double* w_sub, double* w_out,
+                           int64_t n2, bool real_dot, double* part, int nblocks, cudaStream_t st) {
+  if ((w_sub == nullptr) != (w_out == nullptr)) return fail(HZ_ERR_INVALID_ARG, "multi_dot: w_sub and w_out go together");
+  const int64_t nc = n2 / 2;
+  const int chunk = (int)((nc + nblocks - 1) / nblocks);
+  const size_t smem = (size_t)chunk * sizeof(double2);
+  if (real_dot)
+    return w_sub ? launch_multi_dot_T<true, true>(V, ld, nv, w, w_sub, w_out, nc, chunk, smem, part, nblocks, st)
+                 : launch_multi_dot_T<true, false>(V, ld, nv, w, w_sub, w_out, nc, chunk, smem, part, nblocks, st);
+  return w_sub ? launch_multi_dot_T<false, true>(V, ld, nv, w, w_sub, w_out, nc, chunk, smem, part, nblocks, st)
+               : launch_multi_dot_T<false, false>(V, ld, nv, w, w_sub, w_out, nc, chunk, smem, part, nblocks, st);
+}
+
+int axpy_blocks(int64_t n2) { return grid_for(n2 / 2, 256); }
+
 hz_status launch_multi_axpy(const double* V, int64_t ld, int nv, const double* h, double* w, int64_t n2,
-                            bool real_coef, cudaStream_t st) {
-  const int g = grid_for(n2 / 2, 256);
-  multi_axpy_kernel<<<g, 256, (size_t)2 * nv * sizeof(double), st>>>(V, ld, nv, h, w, n2, real_coef ? 1 : 0);
+                            bool real_coef, cudaStream_t st, double* norm_part) {
+  const int64_t nc = n2 / 2;
+  const int g = axpy_blocks(n2);
+  const size_t smem = (size_t)2 * nv * sizeof(double);
+  if (smem > 48 * 1024) {
+    // nv above 3072 basis vectors: not reachable with the restart bound, refuse rather than launch
+    return fail(HZ_ERR_UNSUPPORTED, "multi_axpy: too many basis vectors");
+  }
+  if (real_coef) {
+    if (norm_part) multi_axpy_kernel<true, true><<<g, 256, smem, st>>>(V, ld, nv, h, w, nc, norm_part);
+    else multi_axpy_kernel<true, false><<<g, 256, smem, st>>>(V, ld, nv, h, w, nc, nullptr);
+  } else {
+    if (norm_part) multi_axpy_kernel<false, true><<<g, 256, smem, st>>>(V, ld, nv, h, w, nc, norm_part);
+    else multi_axpy_kernel<false, false><<<g, 256, smem, st>>>(V, ld, nv, h, w, nc, nullptr);
+  }
   note_launch();
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;

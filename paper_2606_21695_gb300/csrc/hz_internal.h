@@ -177,17 +177,21 @@ hz_status launch_assemble_add(const AssembleArgs& a, const double* u_sub, double
 // ---- FP64 vector kernels for the outer Krylov iteration (complex, interleaved)
 // part[blk][2k..2k+1] = partial sum over this block of conj(V_k) . w (complex) or
 // real dot (real_dot = true, imaginary part 0), k = 0..nv-1; V_k = V + k*ld.
+// With w_sub and w_out non-null the kernel dots x = w - w_sub instead and
+// writes x to w_out (the Arnoldi vector (I - S) v from v and S v; w_out must
+// not overlap V_0..V_{nv-1} or w).
 int vec_blocks(int64_t n2);
-hz_status launch_multi_dot(const double* V, int64_t ld, int nv, const double* w, int64_t n2, bool real_dot,
-                           double* part, int nblocks, cudaStream_t st);
-// w -= sum_k h[k] V_k  (h complex on device, nv entries)
+hz_status launch_multi_dot(const double* V, int64_t ld, int nv, const double* w, const double* w_sub, double* w_out,
+                           int64_t n2, bool real_dot, double* part, int nblocks, cudaStream_t st);
+// w -= sum_k h[k] V_k  (h complex on device, nv entries).  With norm_part
+// non-null each block also writes the partial ||w_new||^2 to norm_part[2 blk]
+// (0 to norm_part[2 blk + 1]) and *nblocks receives the block count.
+int axpy_blocks(int64_t n2);
 hz_status launch_multi_axpy(const double* V, int64_t ld, int nv, const double* h, double* w, int64_t n2,
-                            bool real_coef, cudaStream_t st);
-// y = alpha * x (alpha real, on device at *alpha_inv as 1/alpha); y may alias x
-hz_status launch_scale(const double* x, const double* norm, double* y, int64_t n2, cudaStream_t st);
+                            bool real_coef, cudaStream_t st, double* norm_part = nullptr);
 // y = x / sqrt(*norm2) with norm2 in device memory (0 if the norm is 0)
 hz_status launch_scale_inv_norm(const double* x, const double* norm2, double* y, int64_t n2, cudaStream_t st);
-// y = x - y  (for r = g - (I - S) lam: helper)   y = a*x + b*y
+// y = a*x + b*y
 hz_status launch_axpby(double a, const double* x, double b, double* y, int64_t n2, cudaStream_t st);
 
 }  // namespace hz

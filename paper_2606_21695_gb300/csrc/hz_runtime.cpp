@@ -536,12 +536,14 @@ hz_status fetch(Ctx& c, int nd, double* host, int* flags_host) {
   return HZ_OK;
 }
 
-// out[0..2nv) = reduced dots of V_0..V_{nv-1} with w (device small buffer at offset off).
-hz_status dots_to(Ctx& c, const double* V, int64_t ld, int nv, const double* w, bool real, double* out) {
+// out[0..2nv) = reduced dots of V_0..V_{nv-1} with w, or with w - w_sub
+// (then also written to w_out).
+hz_status dots_to(Ctx& c, const double* V, int64_t ld, int nv, const double* w, bool real, double* out,
+                  const double* w_sub = nullptr, double* w_out = nullptr) {
   Problem& pr = c.pr;
   const int nb = vec_blocks(c.n2);
   HZ_TRY(pr.part.ensure((size_t)nb * nv * 2 * sizeof(double) + 64));
-  HZ_TRY(launch_multi_dot(V, ld, nv, w, c.n2, real, pr.part.as<double>(), nb, c.st));
+  HZ_TRY(launch_multi_dot(V, ld, nv, w, w_sub, w_out, c.n2, real, pr.part.as<double>(), nb, c.st));
   return launch_reduce_partials(pr.part.as<double>(), nb, 2 * nv, out, c.st);
 }
 
@@ -645,20 +647,20 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
         double* hd = pr.hcol.as<double>();
         double* hh = pr.hcol_host.as<double>();
         // the step's vector work after its sweep (a fixed sequence of launches
-        // for a given j: captured as a CUDA graph with opts.graphs)
+        // for a given j: captured as a CUDA graph with opts.graphs):
+        // w = v_j - S v_j with the pass-1 dots, pass-1 update, pass-2 dots,
+        // pass-2 update with ||w||^2, normalisation
         auto post = [&](int j) -> hz_status {
           double* vj = V + (size_t)j * n2;
           double* w = V + (size_t)(j + 1) * n2;
-          HZ_CUDA(cudaMemcpyAsync(w, vj, vb, cudaMemcpyDeviceToDevice, c.st));
-          HZ_TRY(launch_axpby(-1.0, tv, 1.0, w, n2, c.st));  // w = v_j - S v_j
           const int nv = j + 1;
           double* col = hd + (size_t)j * CS;
-          HZ_TRY(dots_to(c, V, n2, nv, w, real, col));
+          HZ_TRY(dots_to(c, V, n2, nv, vj, real, col, tv, w));
           HZ_TRY(launch_multi_axpy(V, n2, nv, col, w, n2, real, c.st));
           HZ_TRY(dots_to(c, V, n2, nv, w, real, col + 2 * (m + 2)));
-          HZ_TRY(launch_multi_axpy(V, n2, nv, col + 2 * (m + 2), w, n2, real, c.st));
           double* nrm = col + 2 * (m + 2) + 2 * (m + 1);
-          HZ_TRY(dots_to(c, w, 0, 1, w, real, nrm));
+          HZ_TRY(launch_multi_axpy(V, n2, nv, col + 2 * (m + 2), w, n2, real, c.st, pr.part.as<double>()));
+          HZ_TRY(launch_reduce_partials(pr.part.as<double>(), axpy_blocks(n2), 2, nrm, c.st));
           HZ_TRY(launch_scale_inv_norm(w, nrm, w, n2, c.st));
           double* hslot = hh + (size_t)j * (CS + 4);
           HZ_CUDA(cudaMemcpyAsync(hslot, col, CS * sizeof(double), cudaMemcpyDeviceToHost, c.st));
@@ -674,9 +676,10 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
           return HZ_OK;
         };
         const bool graphs = c.o.graphs && !is_default_stream(c.st);  // default streams cannot be captured
+        // partials of the dots (up to m + 1 vectors) and of the norm; allocated
+        // before any step (and before a capture, which must not allocate)
+        HZ_TRY(pr.part.ensure((size_t)std::max(vec_blocks(n2) * (m + 1), axpy_blocks(n2)) * 2 * sizeof(double) + 64));
         if (graphs) {
-          // every buffer the captured work touches exists before the capture
-          HZ_TRY(pr.part.ensure((size_t)vec_blocks(n2) * (m + 1) * 2 * sizeof(double) + 64));
           const std::vector<const void*> key = {V, tv, hd, hh, pr.flags.ptr, pr.part.ptr, (const void*)(intptr_t)n2,
                                                 (const void*)(intptr_t)m, (const void*)(intptr_t)real};
           if (key != pr.step_graph_key) {
