@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--wh-iters", type=int, default=20, help="WaveHoltz iterations per sweep")
     ap.add_argument("--max-sweeps", type=int, default=5000)
     ap.add_argument("--max-refine", type=int, default=20)
+    ap.add_argument("--gs-passes", type=int, choices=[1, 2], default=1,
+                    help="classical Gram-Schmidt passes per Arnoldi step")
     ap.add_argument("--robin", default="0,1", help="interface condition d_n + k (eta - i zeta): 'eta,zeta'")
     ap.add_argument("--workload", choices=["cfg1", "cfg2", "cfg3", "cfg3s"], default="cfg2",
                     help="cfg2 is the benchmark workload; cfg1/cfg3 are reported separately; cfg3s is the "
@@ -220,7 +222,8 @@ def run_ours(args):
     n = case.n
     stream = torch.cuda.current_stream()
     opts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, inner_tol=1e-2, wh_iters=args.wh_iters,
-                              gmres_restart=60, max_sweeps=args.max_sweeps, max_refine=args.max_refine)
+                              gmres_restart=60, max_sweeps=args.max_sweeps, max_refine=args.max_refine,
+                              gs_passes=args.gs_passes)
     u = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
@@ -295,7 +298,8 @@ def run_ours(args):
         fp64 = None
         if not args.no_fp64:
             o64 = hz.hz_default_opts(precision=hz.HZ_FP64, tol=TOL, inner_tol=1e-2, wh_iters=args.wh_iters,
-                                     gmres_restart=60, max_sweeps=args.max_sweeps, max_refine=args.max_refine)
+                                     gmres_restart=60, max_sweeps=args.max_sweeps, max_refine=args.max_refine,
+                                     gs_passes=args.gs_passes)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -337,7 +341,7 @@ def run_ours(args):
             "config": {"workload": wl.name, "mesh": f"{wl.nx}x{wl.ny} quads", "degree": P,
                        "subdomains": f"{wl.nx // wl.sub_nx}x{wl.ny // wl.sub_ny} of {wl.sub_nx}x{wl.sub_ny}",
                        "omega": wl.omega, "nt": nt, "wh_iters": opts.wh_iters, "tol": TOL,
-                       "outer": "GMRES(60) in FP64 defect correction", "l2": "flushed (256 MB write) before each step",
+                       "outer": f"GMRES(60), {args.gs_passes} classical Gram-Schmidt pass(es), in FP64 defect correction", "l2": "flushed (256 MB write) before each step",
                        "transmission": {"eta": robin[0], "zeta": robin[1]},
                        "parallelism": f"{world} independent solves (one per GPU)"},
             "time_to_tol_s": {"fp32_refine": elapsed / args.steps, "fp64": fp64["seconds"] if fp64 else None},

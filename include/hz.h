@@ -121,6 +121,12 @@ typedef struct {
                             updates, norm, normalisation, read-back of the Hessenberg column -- is
                             captured once per step index as a CUDA graph and replayed in later
                             cycles (one launch instead of about ten per step) */
+  int32_t gs_passes;     /* classical Gram-Schmidt passes per Arnoldi step (Sec. 3's Krylov
+                            acceleration): 1 = one pass (half the FP64 work; orthogonality is lost
+                            gradually over a restart cycle, which can cost iterations but not accuracy:
+                            every DD solve is a correction that the FP64 refinement loop checks
+                            against the true residual), 2 = one pass plus a full reorthogonalisation
+                            (basis orthogonal to rounding).  Other values: HZ_ERR_INVALID_ARG. */
 } hz_solve_opts;
 
 typedef struct {
@@ -141,7 +147,7 @@ typedef struct {
 
 /* Defaults: FP64, tol 1e-8, 2000 sweeps, GMRES(60), 20 WaveHoltz iterations,
  * no wh_tol, CFL 0.9, inner_tol 1e-2, 20 refinements, autotune, pack and
- * graphs on. */
+ * graphs on, one Gram-Schmidt pass. */
 HZ_API void hz_default_opts(hz_solve_opts* opts);
 
 /* Copies the calling thread's last error message (NUL-terminated, truncated

@@ -39,7 +39,7 @@ class hz_solve_opts(C.Structure):
                 ("gmres_restart", C.c_int32), ("wh_iters", C.c_int32), ("wh_tol", C.c_double),
                 ("nt_override", C.c_int32), ("cfl", C.c_double), ("inner_tol", C.c_double),
                 ("max_refine", C.c_int32), ("autotune", C.c_int32), ("wh_adaptive", C.c_int32),
-                ("pack", C.c_int32), ("graphs", C.c_int32)]
+                ("pack", C.c_int32), ("graphs", C.c_int32), ("gs_passes", C.c_int32)]
 
 
 class hz_solve_report(C.Structure):

@@ -648,18 +648,22 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
         double* hh = pr.hcol_host.as<double>();
         // the step's vector work after its sweep (a fixed sequence of launches
         // for a given j: captured as a CUDA graph with opts.graphs):
-        // w = v_j - S v_j with the pass-1 dots, pass-1 update, pass-2 dots,
-        // pass-2 update with ||w||^2, normalisation
+        // w = v_j - S v_j with the pass-1 dots, pass-1 update, [pass-2 dots,
+        // pass-2 update,] the last update with ||w||^2, normalisation
+        const bool two_pass = c.o.gs_passes == 2;
         auto post = [&](int j) -> hz_status {
           double* vj = V + (size_t)j * n2;
           double* w = V + (size_t)(j + 1) * n2;
           const int nv = j + 1;
           double* col = hd + (size_t)j * CS;
-          HZ_TRY(dots_to(c, V, n2, nv, vj, real, col, tv, w));
-          HZ_TRY(launch_multi_axpy(V, n2, nv, col, w, n2, real, c.st));
-          HZ_TRY(dots_to(c, V, n2, nv, w, real, col + 2 * (m + 2)));
           double* nrm = col + 2 * (m + 2) + 2 * (m + 1);
-          HZ_TRY(launch_multi_axpy(V, n2, nv, col + 2 * (m + 2), w, n2, real, c.st, pr.part.as<double>()));
+          HZ_TRY(dots_to(c, V, n2, nv, vj, real, col, tv, w));
+          if (two_pass) {
+            HZ_TRY(launch_multi_axpy(V, n2, nv, col, w, n2, real, c.st));
+            HZ_TRY(dots_to(c, V, n2, nv, w, real, col + 2 * (m + 2)));
+          }
+          HZ_TRY(launch_multi_axpy(V, n2, nv, two_pass ? col + 2 * (m + 2) : col, w, n2, real, c.st,
+                                   pr.part.as<double>()));
           HZ_TRY(launch_reduce_partials(pr.part.as<double>(), axpy_blocks(n2), 2, nrm, c.st));
           HZ_TRY(launch_scale_inv_norm(w, nrm, w, n2, c.st));
           double* hslot = hh + (size_t)j * (CS + 4);
@@ -681,7 +685,8 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
         HZ_TRY(pr.part.ensure((size_t)std::max(vec_blocks(n2) * (m + 1), axpy_blocks(n2)) * 2 * sizeof(double) + 64));
         if (graphs) {
           const std::vector<const void*> key = {V, tv, hd, hh, pr.flags.ptr, pr.part.ptr, (const void*)(intptr_t)n2,
-                                                (const void*)(intptr_t)m, (const void*)(intptr_t)real};
+                                                (const void*)(intptr_t)m, (const void*)(intptr_t)real,
+                                                (const void*)(intptr_t)two_pass};
           if (key != pr.step_graph_key) {
             release_step_graphs(pr);
             pr.step_graph_key = key;
@@ -736,8 +741,9 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
           if (fl[0] & 1) return fail(HZ_ERR_DIVERGED, "non-finite values in the subdomain solve (time step too large?)");
           c.rep.gmres_iters++;
           for (int i = 0; i <= j; ++i)
-            H[(size_t)i * m + j] = cplx(hslot[2 * i] + hslot[2 * (m + 2) + 2 * i],
-                                        hslot[2 * i + 1] + hslot[2 * (m + 2) + 2 * i + 1]);
+            H[(size_t)i * m + j] = two_pass ? cplx(hslot[2 * i] + hslot[2 * (m + 2) + 2 * i],
+                                                   hslot[2 * i + 1] + hslot[2 * (m + 2) + 2 * i + 1])
+                                            : cplx(hslot[2 * i], hslot[2 * i + 1]);
           const double hn2 = hslot[2 * (m + 2) + 2 * (m + 1)];
           const double hnext = std::sqrt(std::max(0.0, hn2));
           // ||(I - S) v|| for a unit v is O(1) for a stable subdomain solve; growth by
@@ -808,6 +814,7 @@ hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report*
       !(o.cfl > 0.0) || o.max_refine < 0 || !(o.inner_tol >= 0.0) || !(o.wh_tol >= 0.0))
     return fail(HZ_ERR_INVALID_ARG, "invalid solve options");
   if (o.outer < HZ_OUTER_GMRES || o.outer > HZ_OUTER_RGMRES) return fail(HZ_ERR_INVALID_ARG, "unknown outer");
+  if (o.gs_passes != 1 && o.gs_passes != 2) return fail(HZ_ERR_INVALID_ARG, "gs_passes must be 1 or 2");
   hz_solve_report rep{};
   const int nt = o.nt_override > 0 ? o.nt_override : choose_nt(pr, o.cfl);
   rep.nt = nt;
@@ -1000,6 +1007,7 @@ void hz_default_opts(hz_solve_opts* o) {
   o->autotune = 1;
   o->pack = 1;
   o->graphs = 1;
+  o->gs_passes = 1;
 }
 
 hz_status hz_last_error(char* buf, size_t n) {

@@ -12,7 +12,8 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("outer", ["gmres", "rgmres"])
-def test_graphs_replay_the_same_launches(hz, outer):
+@pytest.mark.parametrize("gs_passes", [1, 2])
+def test_graphs_replay_the_same_launches(hz, outer, gs_passes):
     from paper_2606_21695_gb300.api import Case
 
     case = Case(configs.Workload("gr", (0, 1, 0, 1), 16, 16, 3, 4, 4, 17.0, "channel", (0.45, 0.3), 0.03))
@@ -21,7 +22,8 @@ def test_graphs_replay_the_same_launches(hz, outer):
     # the first solve of a shape also runs the autotuner: keep it out of the counts
     hz.hz_solve(case.pr, hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=1e-8, outer=out), n=case.n)
     for graphs in (0, 1, 1):  # the second graphs=1 solve replays the cached graphs
-        o = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=1e-8, gmres_restart=12, outer=out, graphs=graphs)
+        o = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=1e-8, gmres_restart=12, outer=out, graphs=graphs,
+                               gs_passes=gs_passes)
         k0 = hz.hz_kernel_launches()
         st, u, rep = hz.hz_solve(case.pr, o, n=case.n)
         assert st == hz.HZ_OK and rep["rel_residual"] <= 1e-8
