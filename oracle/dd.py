@@ -71,18 +71,23 @@ class Problem:
         self.g = {k: np.asarray(v, dtype=complex) for k, v in g.items()}
         if np.any(~np.isfinite(self.c)) or np.any(self.c <= 0):
             raise ValueError("wave speed must be finite and positive")
-        m = mesh
+        self.W2, Hw = self._global_weights()
+        self.Mdiag = self.W2 / self.c**2
+        self.Hdiag = Hw / self.c
+        self._sub_setup()
+
+    def _global_weights(self):
+        """Lumped node weights W (the GLL rule's sum of w_a w_b |J| over the
+        elements at a node) and outer-boundary edge weights, (NY, NX) each."""
+        m = self.mesh
         self.Wx = m.lumped_1d(m.nx, m.hx)
         self.Wy = m.lumped_1d(m.ny, m.hy)
-        self.W2 = np.outer(self.Wy, self.Wx)
         Hw = np.zeros((m.NY, m.NX))
         Hw[0, :] += self.Wx
         Hw[-1, :] += self.Wx
         Hw[:, 0] += self.Wy
         Hw[:, -1] += self.Wy
-        self.Mdiag = self.W2 / self.c**2
-        self.Hdiag = Hw / self.c
-        self._sub_setup()
+        return np.outer(self.Wy, self.Wx), Hw
 
     # ------------------------------------------------------------ global --
     def rhs(self):
@@ -121,9 +126,7 @@ class Problem:
         jj, ii = np.meshgrid(np.arange(m.nly), np.arange(m.nlx), indexing="ij")
         self.gJ = self.oy[:, None, None] + jj[None]  # (L, nly, nlx) global row
         self.gI = self.ox[:, None, None] + ii[None]  # global column
-        self.Wxs = m.lumped_1d(m.sub_nx, m.hx)
-        self.Wys = m.lumped_1d(m.sub_ny, m.hy)
-        Ws = np.outer(self.Wys, self.Wxs)
+        Ws = self._sub_weights()  # (1 or L, nly, nlx)
         # neighbours and interface flags per edge
         self.nbr = -np.ones((L, 4), dtype=int)
         for l in range(L):
@@ -142,15 +145,24 @@ class Problem:
         for e in range(4):
             rows, cols, wts = self.edge_nodes(e)
             for l in range(L):
-                (Hif if self.nbr[l, e] >= 0 else Hout)[l, rows, cols] += wts
+                (Hif if self.nbr[l, e] >= 0 else Hout)[l, rows, cols] += wts[l] if np.ndim(wts) == 2 else wts
         self.c_sub = self.c[self.gJ, self.gI]
-        self.M_sub = Ws[None] / self.c_sub**2
+        self.M_sub = Ws / self.c_sub**2
         self.H_sub = (Hout + self.zeta * Hif) / self.c_sub          # damping: outer impedance, zeta on interfaces
         self.Hm_sub = self.omega * self.eta * Hif / self.c_sub      # interface boundary mass (eta)
-        self.share = Ws[None] / self.W2[self.gJ, self.gI]  # lumped-mass share of each copy
+        self.share = Ws / self.W2[self.gJ, self.gI]  # lumped-mass share of each copy
+
+    def _sub_weights(self):
+        """Lumped node weights of a subdomain's own elements, (1, nly, nlx)
+        (the same for every subdomain of a uniform mesh)."""
+        m = self.mesh
+        self.Wxs = m.lumped_1d(m.sub_nx, m.hx)
+        self.Wys = m.lumped_1d(m.sub_ny, m.hy)
+        return np.outer(self.Wys, self.Wxs)[None]
 
     def edge_nodes(self, e):
-        """(rows, cols, weights) of subdomain edge e in local node indices."""
+        """(rows, cols, weights) of subdomain edge e in local node indices
+        (weights (n,) shared by all subdomains, or (L, n) per subdomain)."""
         m = self.mesh
         if e == EDGE_W:
             return np.arange(m.nly), np.zeros(m.nly, int), self.Wys
@@ -209,7 +221,8 @@ class Problem:
             rows, cols, wts = self.edge_nodes(e)
             n = len(rows)
             for l in np.where(self.nbr[:, e] >= 0)[0]:
-                b[l, rows, cols] += wts * lam_in[l, e, :n]  # <lambda, phi> on the interface
+                wl = wts[l] if np.ndim(wts) == 2 else wts
+                b[l, rows, cols] += wl * lam_in[l, e, :n]  # <lambda, phi> on the interface
         sel = np.arange(m.L) if subset is None else np.asarray(subset, dtype=int)
         u = np.zeros_like(b)
         if inner == "direct":
@@ -262,7 +275,9 @@ class Problem:
             out[k] = spla.spsolve(self.sub_matrix(l), b[k].ravel()).reshape(b[k].shape)
         return out
 
-    def apply_A_sub(self, p):
+    def apply_A_sub(self, p, subs=None):
+        """A p on subdomain arrays p (len(subs) or L, nly, nlx); a uniform
+        mesh has one subdomain operator, so subs is not needed here."""
         m = self.mesh
         return stiffness_apply(p, m.P, m.D, m.w, m.hx, m.hy, m.sub_nx, m.sub_ny)
 
@@ -294,7 +309,7 @@ class Problem:
             v = kappa(0) * p + (1j / w) * kappa(0.5) * pd
             for nu in range(1, last + 1):
                 p = p + sigma * pd
-                Ap = self.apply_A_sub(p) + Hm * p  # interface boundary mass (zero unless eta != 0)
+                Ap = self.apply_A_sub(p, subs) + Hm * p  # interface boundary mass (zero unless eta != 0)
                 force = (b * np.exp(-2j * math.pi * nu / Nt)).real
                 pd = alpha * pd + beta * (-Ap + force)
                 v = v + kappa(nu) * p + (1j / w) * kappa(nu + 0.5) * pd

@@ -59,3 +59,19 @@ def random_speed(gx, gy, corr_len=0.05, seed=3, amp=0.5, clip=1.5):
     """c = 1 + amp * clip(g, -clip, clip) for the random field g above."""
     g = np.clip(random_field(gx, gy, corr_len, seed), -clip, clip)
     return 1.0 + amp * g
+
+
+def warp_nodes(X, Y, box, amp):
+    """Smooth interior distortion of a node grid on the rectangle box =
+    (x0, x1, y0, y1): with s, t the normalised coordinates in [0, 1],
+      x += amp (x1 - x0) sin(2 pi s) sin(pi t),  y += amp (y1 - y0) sin(pi s) sin(2 pi t).
+    Boundary nodes stay on their edges (both terms vanish there), so outer
+    normals and edge data are those of the rectangle; the elements become
+    curved quadrilaterals (orientation kept for amp < 1 / (2 pi (1 + pi/2))).
+    """
+    x0, x1, y0, y1 = box
+    s = (np.asarray(X) - x0) / (x1 - x0)
+    t = (np.asarray(Y) - y0) / (y1 - y0)
+    Xw = X + amp * (x1 - x0) * np.sin(2 * math.pi * s) * np.sin(math.pi * t)
+    Yw = Y + amp * (y1 - y0) * np.sin(math.pi * s) * np.sin(2 * math.pi * t)
+    return Xw, Yw
