@@ -88,12 +88,21 @@ typedef enum {
   HZ_BOUNDARY = 3,   /* 2*(nx*P+1) + 2*(ny*P+1) complex values of g on the outer
                         edges in the order S, E, N, W, each along increasing x
                         (S, N) or y (E, W); corners carry one value per edge */
-  HZ_TRANSMISSION = 4 /* 2 real values (eta >= 0, zeta > 0): the interface condition
+  HZ_TRANSMISSION = 4, /* 2 real values (eta >= 0, zeta > 0): the interface condition
                         B = d_n + k (eta - i zeta) used between subdomains (default
                         eta = 0, zeta = 1: B = d_n - i k, Sec. 3); eta > 0 adds a
                         boundary mass that damps evanescent interface modes (the
                         improved transmission conditions of Sec. 8).  The converged
                         solution does not depend on it, only the iteration count. */
+  HZ_NODE_COORDS = 5  /* 2n real values: physical (x, y) of every global node, interleaved,
+                         x-fastest in the mesh's logical node order.  Makes the mesh one of
+                         general convex quadrilaterals (Sec. 4): each element is the
+                         isoparametric degree-P image of the reference square through its
+                         (P+1)^2 nodes; stiffness, lumped mass and boundary weights then
+                         carry the map's metric.  The Jacobian must be positive at every
+                         GLL node (else HZ_ERR_INVALID_ARG).  Subdomains must have at most
+                         1024 nodes; FP64 and FP32-with-refinement solves only.  Without
+                         it the mesh is the Cartesian grid of hz_mesh_create. */
 } hz_field;
 
 typedef struct {
@@ -139,7 +148,7 @@ typedef struct {
   int64_t dof_updates;   /* sum over sweeps of subdomain nodes x (N_t - 1) x WaveHoltz iterations */
   int32_t gmres_iters;   /* total GMRES iterations */
   int32_t sweep_variant; /* kernel of the last sweep: 1 block, 2 warp per subdomain, 3 cluster,
-                            4 packed with other solves, 5 cluster of warp bands */
+                            4 packed with other solves, 5 cluster of warp bands, 6 mapped mesh */
   int32_t sweep_shape;   /* its configuration: warps per subdomain (2), rows per thread in units
                             of the degree (1, 3; 0 = chosen by size) */
   double sweep_seconds;  /* device time of the sweep kernels (CUDA events on the solve's stream) */

@@ -21,7 +21,7 @@ HZ_OK, HZ_ERR_INVALID_ARG, HZ_ERR_OOM, HZ_ERR_CUDA, HZ_ERR_NOT_CONVERGED = 0, 1,
 HZ_ERR_DIVERGED, HZ_ERR_TIMEOUT, HZ_ERR_BUSY, HZ_ERR_NOT_FOUND, HZ_ERR_INTERNAL, HZ_ERR_UNSUPPORTED = 5, 6, 7, 8, 9, 10
 HZ_FP64, HZ_FP32_REFINE, HZ_FP16_TRIAL, HZ_BF16_TRIAL = 0, 1, 2, 3
 HZ_OUTER_GMRES, HZ_OUTER_PLAIN, HZ_OUTER_RGMRES = 0, 1, 2
-HZ_WAVE_SPEED, HZ_OMEGA, HZ_SOURCE, HZ_BOUNDARY, HZ_TRANSMISSION = 0, 1, 2, 3, 4
+HZ_WAVE_SPEED, HZ_OMEGA, HZ_SOURCE, HZ_BOUNDARY, HZ_TRANSMISSION, HZ_NODE_COORDS = 0, 1, 2, 3, 4, 5
 
 STATUS_NAMES = {0: "HZ_OK", 1: "HZ_ERR_INVALID_ARG", 2: "HZ_ERR_OOM", 3: "HZ_ERR_CUDA", 4: "HZ_ERR_NOT_CONVERGED",
                 5: "HZ_ERR_DIVERGED", 6: "HZ_ERR_TIMEOUT", 7: "HZ_ERR_BUSY", 8: "HZ_ERR_NOT_FOUND",
@@ -207,7 +207,7 @@ def hz_problem_create(mesh, device=0):
 
 def hz_problem_set(pr, field, data):
     """data: numpy array (real for HZ_WAVE_SPEED / HZ_OMEGA / HZ_TRANSMISSION, complex for
-    HZ_SOURCE / HZ_BOUNDARY)."""
+    HZ_SOURCE / HZ_BOUNDARY; HZ_NODE_COORDS: real (n, 2) or 2n values x, y per node)."""
     arr = np.atleast_1d(np.asarray(data))
     if field in (HZ_SOURCE, HZ_BOUNDARY):
         count = arr.size

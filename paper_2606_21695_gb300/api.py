@@ -25,9 +25,17 @@ class Case:
         self.gy = xy[::NX, 1].copy()
         self.pr = B.hz_problem_create(self.mesh, device)
         self.c = self.f = self.g = None
+        self.X = self.Y = None
+        if getattr(wl, "warp", 0.0) > 0.0:  # curved quadrilaterals: node positions from the workload
+            self.X, self.Y = wl.node_xy(self.gx, self.gy)
+            B.hz_problem_set(self.pr, B.HZ_NODE_COORDS, np.stack([self.X.ravel(), self.Y.ravel()], axis=1).ravel())
         if fields:
-            self.c = wl.speed(self.gx, self.gy)
-            self.f = wl.source(self.gx, self.gy)
+            if self.X is not None:
+                self.c = wl.speed_at(self.X, self.Y)
+                self.f = wl.source_at(self.X, self.Y)
+            else:
+                self.c = wl.speed(self.gx, self.gy)
+                self.f = wl.source(self.gx, self.gy)
             self.g = wl.boundary()
             B.hz_problem_set(self.pr, B.HZ_WAVE_SPEED, self.c.ravel())
             B.hz_problem_set(self.pr, B.HZ_OMEGA, np.array([wl.omega]))

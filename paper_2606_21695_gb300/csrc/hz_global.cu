@@ -43,7 +43,8 @@ __device__ void block_sum(double (&v)[NV], double* out) {
 }
 
 // ---- leapfrog coefficients (Sec. 5): per subdomain node
-//   M = Wx_i Wy_j / c^2, H = (edge weights over all four subdomain edges) / c
+//   M = W / c^2 (W = Wx_i Wy_j, or the mapped mesh's lumped weight),
+//   H = (edge weights over all four subdomain edges) / c
 //   alpha = (M - theta H)/(M + theta H), beta = sigma/(M + theta H)
 __global__ void prepare_kernel(const __grid_constant__ PrepArgs a) {
   const int l = blockIdx.y;
@@ -53,13 +54,19 @@ __global__ void prepare_kernel(const __grid_constant__ PrepArgs a) {
     const int i = n % a.nlx, j = n / a.nlx;
     const int64_t I = (int64_t)sxi * a.snxP + i, J = (int64_t)syi * a.snyP + j;
     const double c = a.c[J * a.NXg + I];
-    const double M = a.wxs[i] * a.wys[j] / (c * c);
+    // lumped weight and edge weights: products of the 1D tables on a Cartesian
+    // mesh, the map's per-node values on a mapped one
+    const double* E = a.Esub ? a.Esub + (int64_t)l * 4 * a.NE : nullptr;
+    const double W = a.Wsub ? a.Wsub[(int64_t)l * nn + n] : a.wxs[i] * a.wys[j];
+    const double eS = E ? E[2 * a.NE + i] : a.wxs[i], eN = E ? E[3 * a.NE + i] : a.wxs[i];
+    const double eW = E ? E[0 * a.NE + j] : a.wys[j], eE = E ? E[1 * a.NE + j] : a.wys[j];
+    const double M = W / (c * c);
     // impedance damping on every subdomain edge: weight 1 on the outer
     // boundary, zeta on interfaces (the interface condition's d_t part)
     const double fS = syi > 0 ? a.zeta : 1.0, fN = syi < a.Sy - 1 ? a.zeta : 1.0;
     const double fW = sxi > 0 ? a.zeta : 1.0, fE = sxi < a.Sx - 1 ? a.zeta : 1.0;
-    const double Hw = (j == 0 ? fS * a.wxs[i] : 0.0) + (j == a.nly - 1 ? fN * a.wxs[i] : 0.0) +
-                      (i == 0 ? fW * a.wys[j] : 0.0) + (i == a.nlx - 1 ? fE * a.wys[j] : 0.0);
+    const double Hw = (j == 0 ? fS * eS : 0.0) + (j == a.nly - 1 ? fN * eN : 0.0) + (i == 0 ? fW * eW : 0.0) +
+                      (i == a.nlx - 1 ? fE * eE : 0.0);
     const double H = Hw / c;
     const double den = M + a.theta * H;
     const double be = a.sigma / den;
@@ -207,8 +214,9 @@ __global__ void reduce_partials_kernel(const double* __restrict__ part, int nblo
   if (threadIdx.x == 0) out[k] = res[0];
 }
 
-// u += average of the subdomain copies at every global node (share 1/count
-// per copy: 1, 1/2 on interfaces, 1/4 at cross points; uniform mesh).
+// u += average of the subdomain copies at every global node, weighted by the
+// lumped-mass share of each copy (1/count on a uniform mesh: 1, 1/2 on
+// interfaces, 1/4 at cross points; a.share on a mapped mesh).
 __global__ void assemble_add_kernel(const __grid_constant__ AssembleArgs a, const double* __restrict__ u_sub,
                                     double* __restrict__ u) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
@@ -220,7 +228,7 @@ __global__ void assemble_add_kernel(const __grid_constant__ AssembleArgs a, cons
   int sy1 = J / a.snyP, sy0 = sy1;
   if (sy1 >= a.Sy) { sy1 = a.Sy - 1; sy0 = sy1; }
   else if (J % a.snyP == 0 && J > 0) sy0 = sy1 - 1;
-  const double share = 1.0 / (double)((sx1 - sx0 + 1) * (sy1 - sy0 + 1));
+  const double uniform = 1.0 / (double)((sx1 - sx0 + 1) * (sy1 - sy0 + 1));
   const int64_t nn = (int64_t)a.nlx * a.nly;
   double sr = 0.0, si = 0.0;
   for (int sy = sy0; sy <= sy1; ++sy)
@@ -228,12 +236,14 @@ __global__ void assemble_add_kernel(const __grid_constant__ AssembleArgs a, cons
       const int l = sy * a.Sx + sx;
       const int i = I - sx * a.snxP, j = J - sy * a.snyP;
       const int64_t k = (int64_t)l * nn + (int64_t)j * a.nlx + i;
-      sr += u_sub[2 * k];
-      si += u_sub[2 * k + 1];
+      const double sh = a.share ? a.share[k] : 1.0;
+      sr += sh * u_sub[2 * k];
+      si += sh * u_sub[2 * k + 1];
     }
+  const double scale = a.share ? 1.0 : uniform;
   const int64_t n = (int64_t)J * a.NXg + I;
-  u[2 * n] += share * sr;
-  u[2 * n + 1] += share * si;
+  u[2 * n] += scale * sr;
+  u[2 * n + 1] += scale * si;
 }
 
 // ---- Krylov vector kernels (vectors of n2 doubles = n2/2 complex values)

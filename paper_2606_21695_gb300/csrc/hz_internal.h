@@ -142,6 +142,10 @@ struct PrepArgs {
   const double* c;      // global
   const double* wxs;
   const double* wys;
+  // mapped meshes: per-node lumped weights [L][nly][nlx] and per-edge-node
+  // arc-length weights [L][4][NE] replace the products of wxs, wys (null: Cartesian)
+  const double* Wsub;
+  const double* Esub;
   double* beta64;
   double* alpha64;
   float* beta32;
@@ -171,8 +175,44 @@ hz_status launch_reduce_partials(const double* part, int nblocks, int width, dou
 
 struct AssembleArgs {
   int nlx, nly, Sx, Sy, NXg, NYg, snxP, snyP;
+  const double* share;  // [L][nly][nlx] lumped-mass share of each copy; null: uniform mesh (1/count)
 };
 hz_status launch_assemble_add(const AssembleArgs& a, const double* u_sub, double* u, cudaStream_t st);
+
+// ---- general convex quadrilaterals (isoparametric map from node coordinates)
+// Element-local arrays are [.., ey, ex, b, a] (b along eta, a along xi) with
+// (P+1)^2 nodes per element; metric entries are w_a w_b (G11, G12, G22).
+struct MappedSweepArgs {
+  SweepArgs base;        // coefficients, tables, lambda, rhs and outputs as for the Cartesian kernels
+  const void* geo;       // [L][sny][snx][(P+1)^2][3] Real
+  const double* wedge;   // [L][4][NE] arc-length GLL weights along the subdomain edges
+  const double* share;   // [L][nly][nlx] lumped-mass share (splits a global right-hand side)
+  int snx, sny;
+  double D[(kMaxP + 1) * (kMaxP + 1)];  // D[q (P+1) + a] = l_a'(xi_q)
+};
+// HZ_ERR_UNSUPPORTED when the subdomain has more than 1024 nodes.
+hz_status launch_sweep_mapped_f32(int P, const MappedSweepArgs& a, int L, cudaStream_t st);
+hz_status launch_sweep_mapped_f64(int P, const MappedSweepArgs& a, int L, cudaStream_t st);
+inline hz_status launch_sweep_mapped(bool fp32, int P, const MappedSweepArgs& a, int L, cudaStream_t st) {
+  return fp32 ? launch_sweep_mapped_f32(P, a, L, st) : launch_sweep_mapped_f64(P, a, L, st);
+}
+
+struct MappedGlobalArgs {
+  int NXg, NYg, nx, ny, P;
+  double omega;
+  double D[(kMaxP + 1) * (kMaxP + 1)];
+  const double* c;
+  const double* geo;     // [ny][nx][(P+1)^2][3] global element metric
+  const double* W;       // [NYg][NXg] lumped weights
+  const double* Hw;      // [NYg][NXg] outer-boundary arc-length weights (sum over the node's outer edges)
+  const double* bw;      // [2 NXg + 2 NYg] outer edge weights in S, E, N, W order (as HZ_BOUNDARY)
+  double* flux;          // [ny][nx][(P+1)^2][4] scratch (F1, F2 of Re u and Im u)
+};
+hz_status launch_rhs_mapped(const MappedGlobalArgs& a, const double* f, const double* gb, double* b, cudaStream_t st);
+// r = b - K u as launch_residual (same partial-sum layout, 2 per block)
+hz_status launch_residual_mapped(const MappedGlobalArgs& a, const double* b, const double* u, double* r, double* part,
+                                 int* nblocks, cudaStream_t st);
+int residual_mapped_blocks(const MappedGlobalArgs& a);
 
 // ---- FP64 vector kernels for the outer Krylov iteration (complex, interleaved)
 // part[blk][2k..2k+1] = partial sum over this block of conj(V_k) . w (complex) or

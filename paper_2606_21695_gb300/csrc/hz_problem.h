@@ -56,6 +56,12 @@ struct hz_problem_s {
   std::vector<cudaGraphExec_t> step_graphs;
   std::vector<long long> step_graph_kernels;
   std::vector<const void*> step_graph_key;
+  // general convex quadrilaterals (HZ_NODE_COORDS): geometry from node coordinates
+  bool mapped = false;
+  double mapped_mu = 0.0;      // element bound of lambda_max(W^-1 A), geometry only
+  std::vector<double> mapped_D;  // (P+1)^2 differentiation matrix
+  hz::DevBuf mgeo64, mgeo32, mWs, mEs, mshare;  // per subdomain
+  hz::DevBuf mgeog, mWg, mHw, mbw, mflux;        // global (residual, right-hand side)
   // per-sweep CUDA events while a solve runs (report.sweep_seconds)
   bool time_sweeps = false;
   size_t ev_used = 0;
@@ -65,7 +71,7 @@ struct hz_problem_s {
 namespace hz {
 using Problem = hz_problem_s;
 constexpr int kVariantAuto = 0, kVariantBlock = 1, kVariantWarp = 2, kVariantCluster = 3, kVariantPacked = 4,
-              kVariantClusterBand = 5;
+              kVariantClusterBand = 5, kVariantMapped = 6;
 int sweep_variant();
 struct Choice {
   int variant;  // kVariantBlock / kVariantWarp / kVariantCluster
@@ -85,6 +91,10 @@ hz_status rhs(Problem& pr, double* b, cudaStream_t st);
 hz_status assemble_add(Problem& pr, const double* u_sub, double* u, cudaStream_t st);
 hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report* rep, cudaStream_t st);
 hz_status check_ready(const Problem& pr);
+// Geometry of a mapped mesh from 2n node coordinates (x, y interleaved):
+// validates J > 0 at every GLL node and uploads the metric and weights.
+hz_status set_node_coords(Problem& pr, const double* xy);
+hz_status copy_mapped(const Problem& src, Problem& dst);
 void release_step_graphs(Problem& pr);
 bool is_default_stream(cudaStream_t s);
 unsigned long long launch_count();

@@ -80,9 +80,10 @@ hz_status HostBuf::ensure(size_t nbytes) {
 // ---------------------------------------------------------- problem ops ----
 int choose_nt(const Problem& pr, double cfl) {
   const Geom& g = pr.g;
-  const double lx = max_eig_1d(g, g.snx, g.hx);
-  const double ly = max_eig_1d(g, g.sny, g.hy);
-  const double lam = pr.cmax * pr.cmax * (lx + ly);
+  // Cartesian: lambda_max(M^-1 A) of the subdomain from its 1D factors;
+  // mapped: the element bound (power iteration per element, 1% margin)
+  const double lam = pr.mapped ? pr.cmax * pr.cmax * pr.mapped_mu * 1.01
+                               : pr.cmax * pr.cmax * (max_eig_1d(g, g.snx, g.hx) + max_eig_1d(g, g.sny, g.hy));
   const double dt_max = cfl * 2.0 / std::sqrt(lam);
   const double T = 2.0 * M_PI / pr.omega;
   const double q = std::ceil(T / dt_max);
@@ -155,6 +156,8 @@ hz_status prepare(Problem& pr, int nt, cudaStream_t st) {
   a.c = pr.c.as<double>();
   a.wxs = pr.wxs.as<double>();
   a.wys = pr.wys.as<double>();
+  a.Wsub = pr.mapped ? pr.mWs.as<double>() : nullptr;
+  a.Esub = pr.mapped ? pr.mEs.as<double>() : nullptr;
   a.beta64 = pr.beta64.as<double>();
   a.alpha64 = pr.alpha64.as<double>();
   a.beta32 = pr.beta32.as<float>();
@@ -411,6 +414,24 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
     pr.ev_used += 2;
     HZ_CUDA(cudaEventRecord(e0, st));
   }
+  // general convex quadrilaterals: the element-form kernel (one variant)
+  if (pr.mapped) {
+    if (trial) return fail(HZ_ERR_UNSUPPORTED, "16-bit trials are not built for mapped meshes");
+    MappedSweepArgs ma{};
+    ma.base = a;
+    ma.geo = fp32 ? pr.mgeo32.ptr : pr.mgeo64.ptr;
+    ma.wedge = pr.mEs.as<double>();
+    ma.share = pr.mshare.as<double>();
+    ma.snx = g.snx;
+    ma.sny = g.sny;
+    for (size_t k = 0; k < pr.mapped_D.size(); ++k) ma.D[k] = pr.mapped_D[k];
+    HZ_TRY(launch_sweep_mapped(fp32, g.P, ma, g.L, st));
+    pr.last_variant = kVariantMapped;
+    pr.last_shape = 0;
+    if (e1) HZ_CUDA(cudaEventRecord(e1, st));
+    pr.sweeps_launched++;
+    return HZ_OK;
+  }
   // A solve running as a member of a packer hands its sweep over: one packed
   // launch per outer step covers the subdomains of every member.
   if (pr.packer && precision == HZ_FP32_REFINE && !(wh_tol > 0.0)) {
@@ -474,8 +495,35 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
   return HZ_OK;
 }
 
+static MappedGlobalArgs mapped_args(const Problem& pr) {
+  const Geom& g = pr.g;
+  MappedGlobalArgs a{};
+  a.NXg = g.NXg;
+  a.NYg = g.NYg;
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.P = g.P;
+  a.omega = pr.omega;
+  for (size_t k = 0; k < pr.mapped_D.size(); ++k) a.D[k] = pr.mapped_D[k];
+  a.c = pr.c.as<double>();
+  a.geo = pr.mgeog.as<double>();
+  a.W = pr.mWg.as<double>();
+  a.Hw = pr.mHw.as<double>();
+  a.bw = pr.mbw.as<double>();
+  a.flux = pr.mflux.as<double>();
+  return a;
+}
+
 hz_status residual(Problem& pr, const double* b, const double* u, double* r, double* norms2_dev, cudaStream_t st) {
   HZ_TRY(check_ready(pr));
+  if (pr.mapped) {
+    const MappedGlobalArgs ma = mapped_args(pr);
+    HZ_TRY(pr.part.ensure((size_t)std::max(residual_mapped_blocks(ma), 1) * 2 * sizeof(double)));
+    int used = 0;
+    HZ_TRY(launch_residual_mapped(ma, b, u, r, pr.part.as<double>(), &used, st));
+    if (norms2_dev) HZ_TRY(launch_reduce_partials(pr.part.as<double>(), used, 2, norms2_dev, st));
+    return HZ_OK;
+  }
   const GlobalArgs a = global_args(pr);
   const int nb = residual_blocks(a);
   HZ_TRY(pr.part.ensure((size_t)std::max(nb, 1) * 2 * sizeof(double)));
@@ -487,6 +535,7 @@ hz_status residual(Problem& pr, const double* b, const double* u, double* r, dou
 
 hz_status rhs(Problem& pr, double* b, cudaStream_t st) {
   HZ_TRY(check_ready(pr));
+  if (pr.mapped) return launch_rhs_mapped(mapped_args(pr), pr.f.as<double>(), pr.gb.as<double>(), b, st);
   const GlobalArgs a = global_args(pr);
   return launch_rhs(a, pr.f.as<double>(), pr.gb.as<double>(), b, st);
 }
@@ -502,6 +551,7 @@ hz_status assemble_add(Problem& pr, const double* u_sub, double* u, cudaStream_t
   a.NYg = g.NYg;
   a.snxP = g.snx * g.P;
   a.snyP = g.sny * g.P;
+  a.share = pr.mapped ? pr.mshare.as<double>() : nullptr;
   return launch_assemble_add(a, u_sub, u, st);
 }
 
@@ -826,7 +876,7 @@ hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report*
   HZ_TRY(pr.hsmall.ensure(8192 * sizeof(double)));
   HZ_TRY(prepare(pr, nt, st));
   HZ_TRY(ensure_flags(pr));
-  pr.autotune = o.autotune != 0 && sweep_variant() == kVariantAuto && o.precision <= HZ_FP32_REFINE;
+  pr.autotune = o.autotune != 0 && sweep_variant() == kVariantAuto && o.precision <= HZ_FP32_REFINE && !pr.mapped;
   if (pr.autotune) HZ_TRY(autotune(pr, o.precision, nt, o.wh_iters, st));
   HZ_CUDA(cudaMemsetAsync(pr.flags.ptr, 0, 64, st));
   HZ_TRY(rhs(pr, pr.bvec.as<double>(), st));
@@ -925,6 +975,7 @@ int64_t field_count(const Geom& g, hz_field f) {
     case HZ_SOURCE: return g.n;
     case HZ_BOUNDARY: return 2 * (int64_t)g.NXg + 2 * (int64_t)g.NYg;
     case HZ_TRANSMISSION: return 2;
+    case HZ_NODE_COORDS: return 2 * g.n;
   }
   return -1;
 }
@@ -969,6 +1020,9 @@ hz_status set_field_host(Problem& pr, hz_field field, const double* data, int64_
       if (!(data[0] >= 0.0) || !(data[1] > 0.0)) return fail(HZ_ERR_INVALID_ARG, "need eta >= 0 and zeta > 0");
       pr.robin_eta = data[0];
       pr.robin_zeta = data[1];
+      break;
+    case HZ_NODE_COORDS:
+      HZ_TRY(set_node_coords(pr, data));
       break;
   }
   pr.version++;
@@ -1114,7 +1168,7 @@ hz_status hz_problem_set_device(hz_problem pr, hz_field field, const double* dat
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     HZ_CUDA(cudaMemcpyAsync(tmp.data(), data, nd * sizeof(double), cudaMemcpyDeviceToHost, st));
     HZ_CUDA(cudaStreamSynchronize(st));
-    if (field == HZ_OMEGA || field == HZ_WAVE_SPEED || field == HZ_TRANSMISSION)
+    if (field == HZ_OMEGA || field == HZ_WAVE_SPEED || field == HZ_TRANSMISSION || field == HZ_NODE_COORDS)
       return set_field_host(*pr, field, tmp.data(), count);
     if (!all_finite(tmp.data(), nd)) return fail(HZ_ERR_INVALID_ARG, "non-finite input");
     DevBuf& dst = field == HZ_SOURCE ? pr->f : pr->gb;
@@ -1229,6 +1283,7 @@ hz_status hz_sweep_packed(const hz_problem* problems, int32_t count, const int32
       Problem& pr = *problems[k];
       if (pr.device != dev) return fail(HZ_ERR_INVALID_ARG, "problem not on the current device");
       const Geom& g = pr.g;
+      if (pr.mapped) return fail(HZ_ERR_UNSUPPORTED, "packed sweeps are built for Cartesian meshes only");
       const int shape = packed_shape_id(g.P, g.sny, g.nlx);
       if (shape < 0) return fail(HZ_ERR_UNSUPPORTED, "subdomain shape has no packed sweep variant");
       HZ_TRY(check_ready(pr));

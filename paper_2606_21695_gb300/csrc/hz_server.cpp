@@ -82,6 +82,7 @@ hz_status clone_problem(const hz_problem_s& src, std::unique_ptr<hz_problem_s>* 
   HZ_TRY(copy(pr->Wyg, src.Wyg));
   HZ_TRY(copy(pr->wxs, src.wxs));
   HZ_TRY(copy(pr->wys, src.wys));
+  HZ_TRY(copy_mapped(src, *pr));
   HZ_CUDA(cudaStreamCreateWithFlags(&pr->stream, cudaStreamNonBlocking));
   *out = std::move(pr);
   return HZ_OK;

@@ -61,6 +61,31 @@ class Workload:
         X, Y = self.grid(gx, gy)
         return fields.gaussian_source(X, Y, self.src_center, self.src_width).astype(complex)
 
+    # ---- meshes of curved quadrilaterals (extra["warp"] = amplitude > 0)
+    @property
+    def warp(self):
+        return float(self.extra.get("warp", 0.0))
+
+    def node_xy(self, gx, gy):
+        """Physical node positions (NY, NX): the Cartesian grid, warped when
+        the workload is a curved-quadrilateral mesh."""
+        X, Y = self.grid(gx, gy)
+        if self.warp > 0.0:
+            X, Y = fields.warp_nodes(X, Y, self.box, self.warp)
+        return X, Y
+
+    def speed_at(self, X, Y):
+        """Wave speed at arbitrary node positions (const and channel kinds)."""
+        if self.speed_kind == "const":
+            return np.ones_like(X)
+        if self.speed_kind == "channel":
+            x0, x1, y0, y1 = self.box
+            return fields.y_channel_speed((X - x0) / (x1 - x0), (Y - y0) / (y1 - y0))
+        raise ValueError(f"speed kind {self.speed_kind!r} is defined on the Cartesian grid only")
+
+    def source_at(self, X, Y):
+        return fields.gaussian_source(X, Y, self.src_center, self.src_width).astype(complex)
+
     def boundary(self):
         """Outer boundary data g: zero (first-order absorbing boundary)."""
         NX, NY = self.nx * self.P + 1, self.ny * self.P + 1
@@ -133,8 +158,26 @@ def config5_arrivals(n_requests=2000, rate=200.0, seed=5, group_prob=0.2, group_
     return out
 
 
+def config2m(amp=0.03):
+    """config2 on curved quadrilaterals: the same element grid with its
+    interior nodes moved by fields.warp_nodes (amplitude 3% of the box), so
+    every element is a different curved quad; boundary nodes stay on the
+    square.  Exercises the element-form (metric) stiffness of Sec. 4."""
+    w = config2()
+    return Workload("cfg2m_256x256_p3_sub8_ychannel_warp3", w.box, w.nx, w.ny, w.P, w.sub_nx, w.sub_ny, w.omega,
+                    w.speed_kind, w.src_center, w.src_width, w.speed_seed, w.corr_len, extra={"warp": amp})
+
+
+def mapped(w: Workload, amp: float, name=None):
+    """The same workload on a warped (curved-quadrilateral) node grid."""
+    extra = dict(w.extra)
+    extra["warp"] = amp
+    return Workload(name or f"{w.name}_warp", w.box, w.nx, w.ny, w.P, w.sub_nx, w.sub_ny, w.omega, w.speed_kind,
+                    w.src_center, w.src_width, w.speed_seed, w.corr_len, extra=extra)
+
+
 def scaled(w: Workload, nx: int, ny: int, sub_nx: Optional[int] = None, sub_ny: Optional[int] = None, name=None):
     """Same physics on a smaller mesh (parity cases the oracle finishes
     quickly); omega and fields are unchanged."""
     return Workload(name or f"{w.name}_scaled{nx}x{ny}", w.box, nx, ny, w.P, sub_nx or w.sub_nx, sub_ny or w.sub_ny,
-                    w.omega, w.speed_kind, w.src_center, w.src_width, w.speed_seed, w.corr_len)
+                    w.omega, w.speed_kind, w.src_center, w.src_width, w.speed_seed, w.corr_len, extra=dict(w.extra))
