@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--gs-passes", type=int, choices=[1, 2], default=1,
                     help="classical Gram-Schmidt passes per Arnoldi step")
     ap.add_argument("--robin", default="0,1", help="interface condition d_n + k (eta - i zeta): 'eta,zeta'")
-    ap.add_argument("--workload", choices=["cfg1", "cfg2", "cfg3", "cfg3s"], default="cfg2",
+    ap.add_argument("--workload", choices=["cfg1", "cfg2", "cfg2m", "cfg3", "cfg3s"], default="cfg2",
                     help="cfg2 is the benchmark workload; cfg1/cfg3 are reported separately; cfg3s is the "
                          "cfg3 physics and subdomain shape on a 256x256 mesh (for profiling)")
     return ap.parse_args()
@@ -146,11 +146,15 @@ def oracle_sample(wl, seconds, nsub_max=1024):
         threadpool_limits = None
     import numpy as np
 
-    from oracle import dd, sem
+    from oracle import dd, geom, sem
 
     m = sem.Mesh(*wl.box, wl.nx, wl.ny, wl.P, wl.sub_nx, wl.sub_ny)
     gx, gy = m.coords_1d()
-    pr = dd.Problem(m, wl.speed(gx, gy), wl.omega, wl.source(gx, gy), wl.boundary())
+    if getattr(wl, "warp", 0.0) > 0.0:
+        X, Y = wl.node_xy(gx, gy)
+        pr = geom.MappedProblem(m, X, Y, wl.speed_at(X, Y), wl.omega, wl.source_at(X, Y), wl.boundary())
+    else:
+        pr = dd.Problem(m, wl.speed(gx, gy), wl.omega, wl.source(gx, gy), wl.boundary())
     nt = pr.choose_nt()
     m_wh = 5
     rhs = pr.rhs()
@@ -181,7 +185,24 @@ def workload(name):
 
     if name == "cfg3s":
         return configs.scaled(configs.config3(), 256, 256, 32, 32, name="cfg3_scaled_256x256_p4_sub32")
-    return {"cfg1": configs.config1, "cfg2": configs.config2, "cfg3": configs.config3}[name]()
+    return {"cfg1": configs.config1, "cfg2": configs.config2, "cfg2m": configs.config2m,
+            "cfg3": configs.config3}[name]()
+
+
+def sweep_flops_per_update(wl):
+    """Algorithmic flops per DOF-update of one sweep kernel.
+    Cartesian (tensor-product) stiffness: F(P) = 2P + 13 FMA.
+    Mapped (element-form) stiffness: per element node 2(P+1) FMA for the
+    reference gradient and 4 for the metric fluxes, per (node, element) pair
+    2(P+1) FMA for the D^T gather, and 7 for the leapfrog and filter updates;
+    with e = element nodes per subdomain node (Ne / n_l) that is
+    e (4(P+1) + 4) + 7 FMA.  flops = 2 FMA."""
+    P = wl.P
+    if getattr(wl, "warp", 0.0) > 0.0:
+        ne = wl.sub_nx * wl.sub_ny * (P + 1) ** 2
+        nl = (wl.sub_nx * P + 1) * (wl.sub_ny * P + 1)
+        return 2.0 * ((ne / nl) * (4 * (P + 1) + 4) + 7)
+    return 2.0 * (2 * P + 13)
 
 
 def combine_ranks(elapsed, work, device):
@@ -269,7 +290,7 @@ def run_ours(args):
     res = [r["rel_residual"] for r in reports]
     nt = reports[0]["nt"]
     P = wl.P
-    flops_per_update = 2 * (2 * P + 13)
+    flops_per_update = sweep_flops_per_update(wl)
     dof_per_launch = dof / sweeps
     avg_launch = sweep_s / sweeps
     achieved = flops_per_update * dof_per_launch / avg_launch / 1e12
@@ -348,13 +369,14 @@ def run_ours(args):
             "fp64_solve": fp64,
             "solve": {"sweeps_per_solve": sweeps / args.steps, "rel_residual_max": max(res),
                       "sweep_kernel": {1: "block", 2: "warp", 3: "cluster", 4: "packed",
-                                       5: "cluster of warp bands"}.get(reports[0]["sweep_variant"]),
+                                       5: "cluster of warp bands", 6: "mapped (element form)"}.get(reports[0]["sweep_variant"]),
                       "refinements": reports[0]["refinements"], "gmres_iters": reports[0]["gmres_iters"],
                       "dof_updates_per_solve": dof / args.steps},
             "roofline": {"kernel": {1: "sweep_kernel (block)",
                                     2: ("sweep_warp_kernel (one warp per subdomain)" if reports[0]["sweep_shape"] <= 1
                                         else f"sweep_band_kernel ({reports[0]['sweep_shape']} warps per subdomain)"),
-                                    3: "sweep_cluster_kernel", 5: "sweep_cband_kernel"}.get(reports[0]["sweep_variant"], "?")
+                                    3: "sweep_cluster_kernel", 5: "sweep_cband_kernel",
+                                    6: "sweep_mapped_kernel (element form, block per subdomain)"}.get(reports[0]["sweep_variant"], "?")
                          + " FP32, one launch = one DD sweep", "bound": "alu",
                          "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS,
@@ -362,7 +384,7 @@ def run_ours(args):
                                                                  and reports[0]["sweep_shape"] == 1) else None,
                          "traffic_unit": "bytes per launch (DRAM, ncu)",
                          "sweep_shape": reports[0]["sweep_shape"],
-                         "algorithmic": f"{flops_per_update} flop/DOF-update x {dof_per_launch:.4g} DOF-updates/launch",
+                         "algorithmic": f"{flops_per_update:.4g} flop/DOF-update x {dof_per_launch:.4g} DOF-updates/launch",
                          "avg_launch_ms": avg_launch * 1e3, "launch_share": sweep_s / elapsed},
             "cpu_baseline": cpu,
             "precision_trials": trials,
@@ -437,7 +459,7 @@ def run_sweeps(args):
     ms = e0.elapsed_time(e1) / max(1, args.sweeps - 1)
     L = wl.nx // wl.sub_nx * (wl.ny // wl.sub_ny)
     dof = L * (wl.sub_nx * wl.P + 1) * (wl.sub_ny * wl.P + 1) * (nt - 1) * args.wh_iters
-    flop = 2 * (2 * wl.P + 13) * dof
+    flop = sweep_flops_per_update(wl) * dof
     case.close()
     return {"mode": "sweep", "workload": wl.name, "sweeps": args.sweeps, "nt": nt, "precision": args.precision,
             "wh_iters": args.wh_iters, "ms_per_sweep": ms if args.sweeps > 1 else None,

@@ -4,23 +4,29 @@
 // elements.
 //
 // Layout inside a block: thread t owns subdomain node t (column t % nlx, row
-// t / nlx) and keeps its p, p-dot, filter sums and coefficients in registers.
-// Each time step:
+// t / nlx) and keeps its p, p-dot, filter sums and coefficients in registers;
+// the (element, local node) pairs are spread over the threads in the same
+// way (thread t takes pairs t, t + blockDim, ...).  Each time step:
 //   1. p += sigma pd, published to shared memory; barrier;
-//   2. element-node phase: for every (element, local node) pair -- threads
-//      stride over them -- the reference gradient (u_xi, u_eta) from P+1
+//   2. per element node: the reference gradient (u_xi, u_eta) from P+1
 //      neighbours each along the element's row and column, and the metric
-//      fluxes F1 = w w (G11 u_xi + G12 u_eta), F2 = w w (G12 u_xi + G22 u_eta)
-//      into shared memory; barrier;
-//   3. node phase: A p at the owned node = sum over the (up to four) elements
-//      containing it of D^T F1 along xi plus D^T F2 along eta (the assembly
-//      of the element contributions as a gather: no atomics), then the
-//      modified-leapfrog update and the filter sums.
-// The per-element-node metric (3 values) is staged in shared memory once per
-// sweep.  Prologue and epilogue (right-hand side from the split global source
-// and the incoming lambda with arc-length edge weights, WaveHoltz stopping
-// test, transmission update into the neighbours' slots) follow the Cartesian
-// block kernel.
+//      fluxes F1 = w w (G11 u_xi + G12 u_eta), F2 = w w (G12 u_xi + G22 u_eta);
+//      barrier;
+//   3. per element node: its element's contribution to A p at that node,
+//      sum_q D[q][a] F1(b, q) + sum_q D[q][b] F2(q, a); barrier;
+//   4. per node: A p = the sum of the contributions of its (up to four)
+//      elements (the assembly as a gather: no atomics), then the modified
+//      leapfrog update and the filter sums.
+// Splitting the contraction (3) from the gather (4) keeps the work per thread
+// the same for every node (a cross point gathers four values, not four
+// contractions); element arrays in shared memory use an odd stride per
+// element so that neighbouring elements fall in different banks.  The metric
+// (3 values per element node) stays in registers when every thread owns at
+// most one element node, else it is read from shared memory.
+// Prologue and epilogue (right-hand side from the split global source and
+// the incoming lambda with arc-length edge weights, WaveHoltz stopping test,
+// transmission update into the neighbours' slots) follow the Cartesian block
+// kernel.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -46,19 +52,26 @@ struct MTab4<double> {
 
 constexpr int kMappedThreads = 1024;
 
+// element stride in shared memory: (P+1)^2 rounded up to an odd count
+template <int P>
+struct MappedStride {
+  static constexpr int value = ((P + 1) * (P + 1)) | 1;
+};
+
 template <typename Real, int P>
 __global__ void __launch_bounds__(kMappedThreads) sweep_mapped_kernel(const __grid_constant__ MappedSweepArgs ma) {
-  constexpr int M = P + 1, N2 = M * M;
+  constexpr int M = P + 1, N2 = M * M, S = MappedStride<P>::value;
   using Tab = typename MTab4<Real>::type;
   const SweepArgs& a = ma.base;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nlx = a.nlx, nly = a.nly, nl = nlx * nly;
   const int snx = ma.snx, sny = ma.sny;
-  const int Ne = snx * sny * N2;
+  const int nel = snx * sny, Ne = nel * N2;
   Real* ps = reinterpret_cast<Real*>(smem_raw);  // [nl]
-  Real* f1 = ps + nl;                            // [Ne]
-  Real* f2 = f1 + Ne;                            // [Ne]
-  Real* geo = f2 + Ne;                           // [Ne][3]
+  Real* f1 = ps + nl;                            // [nel][S]
+  Real* f2 = f1 + nel * S;                       // [nel][S]
+  Real* cc = f2 + nel * S;                       // [nel][S] element contributions to A p
+  Real* geo = cc + nel * S;                      // [Ne][3]
   __shared__ Real Ds[N2];
   __shared__ double red[2 * 32];
   __shared__ int stop_flag;
@@ -72,13 +85,37 @@ __global__ void __launch_bounds__(kMappedThreads) sweep_mapped_kernel(const __gr
   }
   const bool own = t < nl;
   const int i = own ? t % nlx : 0, j = own ? t / nlx : 0;
-  // elements containing the node: in x the one on the left (local index P)
-  // and the one it starts (local index i % P), in y likewise
-  int ex[2], ax[2], nex = 0, ey[2], by[2], ney = 0;
-  if (i % P == 0 && i > 0) { ex[nex] = i / P - 1; ax[nex] = P; ++nex; }
-  if (i / P < snx) { ex[nex] = i / P; ax[nex] = i % P; ++nex; }
-  if (j % P == 0 && j > 0) { ey[ney] = j / P - 1; by[ney] = P; ++ney; }
-  if (j / P < sny) { ey[ney] = j / P; by[ney] = j % P; ++ney; }
+  // element slots of the node's (up to four) elements: in x the one on the
+  // left (local index P) and the one it starts (local index i % P), likewise
+  // in y; unused slots are -1
+  int slot[4] = {-1, -1, -1, -1};
+  if (own) {
+    int ex[2], ax[2], nex = 0, ey[2], by[2], ney = 0;
+    if (i % P == 0 && i > 0) { ex[nex] = i / P - 1; ax[nex] = P; ++nex; }
+    if (i / P < snx) { ex[nex] = i / P; ax[nex] = i % P; ++nex; }
+    if (j % P == 0 && j > 0) { ey[ney] = j / P - 1; by[ney] = P; ++ney; }
+    if (j / P < sny) { ey[ney] = j / P; by[ney] = j % P; ++ney; }
+    int q = 0;
+    for (int qy = 0; qy < ney; ++qy)
+      for (int qx = 0; qx < nex; ++qx) slot[q++] = (ey[qy] * snx + ex[qx]) * S + by[qy] * M + ax[qx];
+  }
+  // the thread's element node when it owns at most one (metric in registers)
+  const bool one_en = Ne <= (int)blockDim.x;
+  const bool own_en = t < Ne;
+  Real g0 = Real(0), g1 = Real(0), g2 = Real(0);
+  int en_e = 0, en_b = 0, en_a = 0;
+  if (own_en) {
+    en_e = t / N2;
+    const int loc = t - en_e * N2;
+    en_b = loc / M;
+    en_a = loc - en_b * M;
+  }
+  __syncthreads();
+  if (one_en && own_en) {
+    g0 = geo[3 * t];
+    g1 = geo[3 * t + 1];
+    g2 = geo[3 * t + 2];
+  }
 
   // ---- per-node coefficients and right-hand side (Algorithm 1 step 1)
   const int64_t nn = (int64_t)nl;
@@ -131,36 +168,59 @@ __global__ void __launch_bounds__(kMappedThreads) sweep_mapped_kernel(const __gr
       p += sigma * pd;
       if (own) ps[t] = p;
       __syncthreads();
-      // element-node phase: metric fluxes
+      // 2. metric fluxes per element node
+      if (one_en) {
+        if (own_en) {
+          const int exe = en_e % snx, eye = en_e / snx;
+          const Real* row = ps + (eye * P + en_b) * nlx + exe * P;
+          const Real* col = ps + (eye * P) * nlx + exe * P + en_a;
+          Real uxi = Real(0), ueta = Real(0);
+#pragma unroll
+          for (int c = 0; c < M; ++c) {
+            uxi += Ds[en_a * M + c] * row[c];
+            ueta += Ds[en_b * M + c] * col[c * nlx];
+          }
+          const int k = en_e * S + en_b * M + en_a;
+          f1[k] = g0 * uxi + g1 * ueta;
+          f2[k] = g1 * uxi + g2 * ueta;
+        }
+      } else {
+        for (int en = t; en < Ne; en += blockDim.x) {
+          const int e = en / N2, loc = en - e * N2;
+          const int b = loc / M, aa = loc - b * M;
+          const int exe = e % snx, eye = e / snx;
+          const Real* row = ps + (eye * P + b) * nlx + exe * P;
+          const Real* col = ps + (eye * P) * nlx + exe * P + aa;
+          Real uxi = Real(0), ueta = Real(0);
+#pragma unroll
+          for (int c = 0; c < M; ++c) {
+            uxi += Ds[aa * M + c] * row[c];
+            ueta += Ds[b * M + c] * col[c * nlx];
+          }
+          const Real* g = geo + 3 * en;
+          f1[e * S + loc] = g[0] * uxi + g[1] * ueta;
+          f2[e * S + loc] = g[1] * uxi + g[2] * ueta;
+        }
+      }
+      __syncthreads();
+      // 3. element contributions D^T F per element node
       for (int en = t; en < Ne; en += blockDim.x) {
         const int e = en / N2, loc = en - e * N2;
         const int b = loc / M, aa = loc - b * M;
-        const int exe = e % snx, eye = e / snx;
-        const Real* row = ps + (eye * P + b) * nlx + exe * P;
-        const Real* col = ps + (eye * P) * nlx + exe * P + aa;
-        Real uxi = Real(0), ueta = Real(0);
+        const Real* F1 = f1 + e * S + b * M;  // F1(b, q)
+        const Real* F2 = f2 + e * S + aa;     // F2(q, aa), stride M
+        Real acc = Real(0);
 #pragma unroll
-        for (int c = 0; c < M; ++c) {
-          uxi += Ds[aa * M + c] * row[c];
-          ueta += Ds[b * M + c] * col[c * nlx];
-        }
-        const Real* g = geo + 3 * en;
-        f1[en] = g[0] * uxi + g[1] * ueta;
-        f2[en] = g[1] * uxi + g[2] * ueta;
+        for (int q = 0; q < M; ++q) acc += Ds[q * M + aa] * F1[q] + Ds[q * M + b] * F2[q * M];
+        cc[e * S + loc] = acc;
       }
       __syncthreads();
-      // node phase: gather D^T F over the node's elements, leapfrog update
+      // 4. gather per node, leapfrog update
       if (own) {
-        Real Ap = Real(0);
-        for (int qy = 0; qy < ney; ++qy)
-          for (int qx = 0; qx < nex; ++qx) {
-            const int e = ey[qy] * snx + ex[qx];
-            const int aa = ax[qx], b = by[qy];
-            const Real* F1 = f1 + e * N2 + b * M;  // F1(b, q), q = 0..P
-            const Real* F2 = f2 + e * N2 + aa;     // F2(r, aa), r = 0..P (stride M)
+        Real Ap = cc[slot[0]];
 #pragma unroll
-            for (int q = 0; q < M; ++q) Ap += Ds[q * M + aa] * F1[q] + Ds[q * M + b] * F2[q * M];
-          }
+        for (int q = 1; q < 4; ++q)
+          if (slot[q] >= 0) Ap += cc[slot[q]];
         pd = alp * pd - bet * Ap + bbr * tb.x + bbi * tb.y + gam * p;
         vre += tb.z * p;
         vim += tb.w * pd;
@@ -259,14 +319,14 @@ __global__ void __launch_bounds__(kMappedThreads) sweep_mapped_kernel(const __gr
 
 template <typename Real, int P>
 hz_status launch_mapped_P(const MappedSweepArgs& a, int L, cudaStream_t st) {
-  constexpr int N2 = (P + 1) * (P + 1);
+  constexpr int N2 = (P + 1) * (P + 1), S = MappedStride<P>::value;
   const int nl = a.base.nlx * a.base.nly;
-  const int Ne = a.snx * a.sny * N2;
+  const int nel = a.snx * a.sny, Ne = nel * N2;
   if (nl > kMappedThreads) return fail(HZ_ERR_UNSUPPORTED, "mapped sweep: subdomain has more than 1024 nodes");
   int threads = nl > Ne ? nl : Ne;
   if (threads > kMappedThreads) threads = kMappedThreads;
   threads = (threads + 31) / 32 * 32;
-  const size_t smem = (size_t)(nl + 5 * (size_t)Ne) * sizeof(Real);
+  const size_t smem = ((size_t)nl + 3 * (size_t)nel * S + 3 * (size_t)Ne) * sizeof(Real);
   if (smem > 200 * 1024) return fail(HZ_ERR_UNSUPPORTED, "mapped sweep: subdomain exceeds shared memory");
   auto kern = sweep_mapped_kernel<Real, P>;
   if (smem > 48 * 1024) HZ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
