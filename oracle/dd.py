@@ -199,7 +199,8 @@ class Problem:
         return max(3, int(math.ceil((2.0 * math.pi / self.omega) / dt_max)))
 
     # ------------------------------------------------------------- sweep --
-    def sweep(self, lam_in, rhs_glob=None, Nt=None, m_wh=5, wh_tol=0.0, want_u=False, inner="waveholtz", subset=None):
+    def sweep(self, lam_in, rhs_glob=None, Nt=None, m_wh=5, wh_tol=0.0, want_u=False, inner="waveholtz", subset=None,
+              u0=None):
         """One DDM cycle (Algorithm 1) on every subdomain.
 
         lam_in: (L, 4, NE) complex, incoming data per subdomain edge (W,E,S,N),
@@ -211,6 +212,8 @@ class Problem:
         subdomain system (isolates the DD fixed point in tests).
         subset: optional list of subdomains to solve (others get u = 0 and
         send nothing); used for sampled checks of large problems.
+        u0: optional (L, nly, nlx) start of the WaveHoltz iteration instead of
+        zero (warm start from a previous sweep's subdomain solutions).
         """
         m = self.mesh
         Nt = self.choose_nt() if Nt is None else Nt
@@ -229,7 +232,7 @@ class Problem:
             u[sel] = self.direct_sub(b[sel], sel)
             iters = np.zeros(m.L, int)
         else:
-            u_sel, it_sel = self.waveholtz(b[sel], Nt, m_wh, wh_tol, subs=sel)
+            u_sel, it_sel = self.waveholtz(b[sel], Nt, m_wh, wh_tol, subs=sel, u0=None if u0 is None else u0[sel])
             u[sel] = u_sel
             iters = np.zeros(m.L, int)
             iters[sel] = it_sel
@@ -327,18 +330,22 @@ class Problem:
 
     # ------------------------------------------------------ outer solves --
     def dd_solve(self, rhs_glob, Nt=None, m_wh=5, wh_tol=0.0, outer="gmres", restart=50, tol=1e-10, max_sweeps=500,
-                 inner="waveholtz"):
+                 inner="waveholtz", warm=False):
         """Approximate K^{-1} rhs_glob by the DD method (one refinement step).
 
         gmres / rgmres: solve (I - S) lam = g with g = sweep(0, rhs), S the
         homogeneous sweep, by complex GMRES / real GMRES on the interleaved
-        (re, im) vector; plain: lam <- sweep(lam, rhs).  A final sweep at lam returns
-        the subdomain solutions, assembled by mass-weighted averaging.
+        (re, im) vector; plain: lam <- sweep(lam, rhs), with warm=True each
+        sweep's WaveHoltz starting from the previous sweep's subdomain
+        solutions.  A final sweep at lam returns the subdomain solutions,
+        assembled by mass-weighted averaging; info["wh_iters"] sums the
+        WaveHoltz iterations of the plain iteration's sweeps and the final one.
         Returns (u_global, info dict with sweeps and residual history)."""
         Nt = self.choose_nt() if Nt is None else Nt
         shape = (self.mesh.L, 4, self.mesh.NE)
         sweeps = 0
-        g = self.sweep(np.zeros(shape, complex), rhs_glob, Nt, m_wh, wh_tol, inner=inner)
+        g, u_first, it = self.sweep(np.zeros(shape, complex), rhs_glob, Nt, m_wh, wh_tol, inner=inner, want_u=True)
+        wh_total = int(np.sum(it))  # WaveHoltz iterations summed over subdomains and sweeps
         sweeps += 1
         hist = []
         if outer == "gmres":
@@ -366,10 +373,20 @@ class Problem:
             sweeps += nmv
             lam = to_c(lam_r)
         elif outer == "plain":
+            # warm: every sweep starts WaveHoltz from the previous sweep's
+            # subdomain solutions (Sec. 8's loose-then-tight inner solves; the
+            # sweep then depends on the previous iterate, so only the plain
+            # fixed-point iteration can use it)
             lam = g
             gn = np.linalg.norm(g)
+            u_prev = u_first if warm else None
             for _ in range(max(0, max_sweeps - 2)):
-                new = self.sweep(lam, rhs_glob, Nt, m_wh, wh_tol, inner=inner)
+                if warm:
+                    new, u_prev, it = self.sweep(lam, rhs_glob, Nt, m_wh, wh_tol, want_u=True, inner=inner, u0=u_prev)
+                    wh_total += int(np.sum(it))
+                else:
+                    new, _, it = self.sweep(lam, rhs_glob, Nt, m_wh, wh_tol, want_u=True, inner=inner)
+                    wh_total += int(np.sum(it))
                 sweeps += 1
                 d = np.linalg.norm(new - lam)
                 lam = new
@@ -378,9 +395,12 @@ class Problem:
                     break
         else:
             raise ValueError(outer)
-        _, u_sub, _ = self.sweep(lam, rhs_glob, Nt, m_wh, wh_tol, want_u=True, inner=inner)
+        _, u_sub, it = self.sweep(lam, rhs_glob, Nt, m_wh, wh_tol, want_u=True, inner=inner,
+                                  u0=u_prev if (outer == "plain" and warm) else None)
+        wh_total += int(np.sum(it))
         sweeps += 1
-        return self.assemble_u(u_sub), {"sweeps": sweeps, "hist": hist, "lam": lam, "u_sub": u_sub}
+        return self.assemble_u(u_sub), {"sweeps": sweeps, "hist": hist, "lam": lam, "u_sub": u_sub,
+                                        "wh_iters": wh_total}
 
     def solve(self, Nt=None, m_wh=5, wh_tol=0.0, tol=1e-8, outer="gmres", restart=50, inner_tol=1e-10,
               max_sweeps=500, max_refine=10, inner="waveholtz"):

@@ -332,3 +332,21 @@ def test_single_subdomain_and_zero_rhs():
     np.testing.assert_allclose(u, pr.direct_solve(), rtol=1e-12, atol=1e-14)
     z, info = pr.dd_solve(0 * pr.rhs())
     assert np.all(z == 0)
+
+
+def test_warm_started_waveholtz_plain_iteration():
+    """Warm start (each sweep's WaveHoltz from the previous sweep's subdomain
+    solutions, plain fixed-point iteration, tolerance-controlled WaveHoltz):
+    the same fixed point -- the global direct solve -- with fewer WaveHoltz
+    iterations than cold starts from zero."""
+    pr = _problem(4, 2, 2, 2, 2, omega=4.0, seed=11)  # two subdomains: the plain iteration converges
+    b = pr.rhs()
+    ud = pr.direct_solve()
+    res = {}
+    for warm in (False, True):
+        u, info = pr.dd_solve(b, outer="plain", m_wh=80, wh_tol=1e-10, tol=1e-7, max_sweeps=300, warm=warm)
+        assert np.max(np.abs(u - ud)) < 1e-5 * np.max(np.abs(ud)), warm
+        res[warm] = info
+    assert res[True]["wh_iters"] < 0.7 * res[False]["wh_iters"], (res[True]["wh_iters"], res[False]["wh_iters"])
+    # the outer iterates agree to the WaveHoltz tolerance, so the sweep counts match
+    assert abs(res[True]["sweeps"] - res[False]["sweeps"]) <= 2
