@@ -136,6 +136,12 @@ typedef struct {
                             every DD solve is a correction that the FP64 refinement loop checks
                             against the true residual), 2 = one pass plus a full reorthogonalisation
                             (basis orthogonal to rounding).  Other values: HZ_ERR_INVALID_ARG. */
+  int32_t wh_warm;       /* 1: each sweep of the plain fixed-point iteration (outer = HZ_OUTER_PLAIN)
+                            starts WaveHoltz from the previous sweep's subdomain solutions instead of
+                            zero (Sec. 8: subdomain solves loose at first, tighter as lambda settles;
+                            with wh_tol > 0 the WaveHoltz iteration count falls as the outer iteration
+                            converges).  The sweep then depends on the previous iterate, so the GMRES
+                            outer iterations refuse it (HZ_ERR_INVALID_ARG).  Default 0. */
 } hz_solve_opts;
 
 typedef struct {
@@ -156,7 +162,7 @@ typedef struct {
 
 /* Defaults: FP64, tol 1e-8, 2000 sweeps, GMRES(60), 20 WaveHoltz iterations,
  * no wh_tol, CFL 0.9, inner_tol 1e-2, 20 refinements, autotune, pack and
- * graphs on, one Gram-Schmidt pass. */
+ * graphs on, one Gram-Schmidt pass, no warm start. */
 HZ_API void hz_default_opts(hz_solve_opts* opts);
 
 /* Copies the calling thread's last error message (NUL-terminated, truncated
@@ -248,6 +254,17 @@ HZ_API hz_status hz_prepare(hz_problem pr, int32_t nt, void* stream);
  * nlx = sub_nx*P+1, subdomain-major).  precision: hz_precision of the loop. */
 HZ_API hz_status hz_sweep(hz_problem pr, int32_t precision, int32_t nt, int32_t wh_iters, double wh_tol,
                    const double* lam_in, double* lam_out, const double* rhs, double* u_sub, void* stream);
+
+/* hz_sweep with WaveHoltz started from u0 instead of zero (the warm start of
+ * opts.wh_warm, Sec. 8): u0 holds subdomain solutions in the u_sub layout
+ * (device, complex, L x nly x nlx), typically the previous sweep's; u0 may be
+ * the same buffer as u_sub (each subdomain reads its start before it writes
+ * its result).  Runs on the one-warp kernel where it fits (FP32), else the
+ * block kernel, or the mapped-mesh kernel.  16-bit trial precisions:
+ * HZ_ERR_UNSUPPORTED. */
+HZ_API hz_status hz_sweep_from(hz_problem pr, int32_t precision, int32_t nt, int32_t wh_iters, double wh_tol,
+                               const double* lam_in, double* lam_out, const double* rhs, const double* u0,
+                               double* u_sub, void* stream);
 
 /* The same sweep for count problems in one packed launch (the batched form
  * used by hz_solve_batch and the server; Algorithm 1, Sec. 6): every

@@ -39,7 +39,8 @@ class hz_solve_opts(C.Structure):
                 ("gmres_restart", C.c_int32), ("wh_iters", C.c_int32), ("wh_tol", C.c_double),
                 ("nt_override", C.c_int32), ("cfl", C.c_double), ("inner_tol", C.c_double),
                 ("max_refine", C.c_int32), ("autotune", C.c_int32), ("wh_adaptive", C.c_int32),
-                ("pack", C.c_int32), ("graphs", C.c_int32), ("gs_passes", C.c_int32)]
+                ("pack", C.c_int32), ("graphs", C.c_int32), ("gs_passes", C.c_int32),
+                ("wh_warm", C.c_int32)]
 
 
 class hz_solve_report(C.Structure):
@@ -88,6 +89,7 @@ def load():
         "hz_lambda_size": (i32, [vp, C.POINTER(i64)]),
         "hz_prepare": (i32, [vp, i32, vp]),
         "hz_sweep": (i32, [vp, i32, i32, i32, d, vp, vp, vp, vp, vp]),
+        "hz_sweep_from": (i32, [vp, i32, i32, i32, d, vp, vp, vp, vp, vp, vp]),
         "hz_sweep_packed": (i32, [C.POINTER(vp), i32, C.POINTER(i32), i32, C.POINTER(vp), C.POINTER(vp),
                                   C.POINTER(vp), C.POINTER(vp), vp]),
         "hz_rhs": (i32, [vp, vp, vp]),
@@ -112,7 +114,7 @@ def exported_names():
     """Names of the C functions this binding expects libhz.so to export."""
     return ["hz_default_opts", "hz_last_error", "hz_kernel_launches", "hz_mesh_create", "hz_mesh_num_nodes", "hz_mesh_node_coords",
             "hz_mesh_destroy", "hz_problem_create", "hz_problem_set", "hz_problem_set_device", "hz_problem_destroy",
-            "hz_problem_nt", "hz_solve", "hz_solve_device", "hz_solve_batch", "hz_lambda_size", "hz_prepare", "hz_sweep",
+            "hz_problem_nt", "hz_solve", "hz_solve_device", "hz_solve_batch", "hz_lambda_size", "hz_prepare", "hz_sweep", "hz_sweep_from",
             "hz_sweep_packed", "hz_rhs",
             "hz_residual", "hz_residual_noalloc", "hz_assemble_add", "hz_server_create", "hz_server_submit", "hz_server_poll",
             "hz_server_stats", "hz_server_destroy"]
@@ -281,6 +283,11 @@ def hz_prepare(pr, nt, stream=None):
 def hz_sweep(pr, precision, nt, wh_iters, wh_tol, lam_in, lam_out, rhs=None, u_sub=None, stream=None):
     _check(load().hz_sweep(pr, precision, nt, wh_iters, wh_tol, _ptr(lam_in), _ptr(lam_out), _ptr(rhs), _ptr(u_sub),
                            _stream(stream)))
+
+
+def hz_sweep_from(pr, precision, nt, wh_iters, wh_tol, lam_in, lam_out, rhs, u0, u_sub=None, stream=None):
+    _check(load().hz_sweep_from(pr, precision, nt, wh_iters, wh_tol, _ptr(lam_in), _ptr(lam_out), _ptr(rhs), _ptr(u0),
+                                _ptr(u_sub), _stream(stream)))
 
 
 def hz_sweep_packed(problems, nts, wh_iters, lam_in, lam_out, rhs=None, u_sub=None, stream=None):

@@ -90,6 +90,7 @@ struct SweepArgs {
   int* wh_iter_max;
   unsigned long long* wh_iter_sum;  // sum over subdomains of WaveHoltz iterations
   int* flags;           // bit 0: non-finite value seen
+  const double* u0;     // [L][nly][nlx] complex or null: WaveHoltz starts from it instead of zero
 };
 
 // Parameters of the warp-per-subdomain FP32 sweep (subdomains <= 32 node

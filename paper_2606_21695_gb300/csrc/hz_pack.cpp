@@ -41,7 +41,7 @@ Packer::~Packer() {
 }
 
 bool Packer::packable(const Problem& pr, const hz_solve_opts& o) {
-  if (o.precision != HZ_FP32_REFINE || o.wh_tol > 0.0 || o.wh_adaptive || pr.mapped) return false;
+  if (o.precision != HZ_FP32_REFINE || o.wh_tol > 0.0 || o.wh_adaptive || o.wh_warm || pr.mapped) return false;
   return packed_shape_id(pr.g.P, pr.g.sny, pr.g.nlx) >= 0;
 }
 

@@ -49,6 +49,7 @@ struct hz_problem_s {
   hz::DevBuf beta64, alpha64, beta32, alpha32, kedge, tab64, tab32;
   // solver workspace
   hz::DevBuf bvec, rvec, uvec, usub, gv, xv, tv, V, part, small, flags, hcol;
+  hz::DevBuf uwarm;  // subdomain solutions carried between sweeps (opts.wh_warm)
   hz::HostBuf hsmall, hcol_host;
   std::vector<cudaEvent_t> gm_events;  // one per Arnoldi step of a cycle
   // CUDA graphs of the Arnoldi step's vector work, one per step index of the
@@ -85,7 +86,8 @@ hz_status autotune(Problem& pr, int precision, int nt, int m_wh, cudaStream_t st
 int choose_nt(const Problem& pr, double cfl);
 hz_status prepare(Problem& pr, int nt, cudaStream_t st);
 hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, const double* lam_in, double* lam_out,
-                const double* rhs, double* u_sub, cudaStream_t st);
+                const double* rhs, double* u_sub, cudaStream_t st,
+                const double* u0 = nullptr);
 hz_status residual(Problem& pr, const double* b, const double* u, double* r, double* norms2_dev, cudaStream_t st);
 hz_status rhs(Problem& pr, double* b, cudaStream_t st);
 hz_status assemble_add(Problem& pr, const double* u_sub, double* u, cudaStream_t st);

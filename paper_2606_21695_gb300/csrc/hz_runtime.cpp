@@ -390,7 +390,7 @@ hz_status autotune(Problem& pr, int precision, int nt, int m_wh, cudaStream_t st
 }
 
 hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, const double* lam_in, double* lam_out,
-                const double* rhs, double* u_sub, cudaStream_t st) {
+                const double* rhs, double* u_sub, cudaStream_t st, const double* u0) {
   HZ_TRY(prepare(pr, nt, st));
   HZ_TRY(ensure_flags(pr));
   const Geom& g = pr.g;
@@ -419,6 +419,7 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
     if (trial) return fail(HZ_ERR_UNSUPPORTED, "16-bit trials are not built for mapped meshes");
     MappedSweepArgs ma{};
     ma.base = a;
+    ma.base.u0 = u0;
     ma.geo = fp32 ? pr.mgeo32.ptr : pr.mgeo64.ptr;
     ma.wedge = pr.mEs.as<double>();
     ma.share = pr.mshare.as<double>();
@@ -434,7 +435,7 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
   }
   // A solve running as a member of a packer hands its sweep over: one packed
   // launch per outer step covers the subdomains of every member.
-  if (pr.packer && precision == HZ_FP32_REFINE && !(wh_tol > 0.0)) {
+  if (pr.packer && precision == HZ_FP32_REFINE && !(wh_tol > 0.0) && !u0) {
     const int shape = packed_shape_id(g.P, g.sny, g.nlx);
     if (shape >= 0) {
       WarpSweepArgs w{};
@@ -454,6 +455,20 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
   // FP32 -> warp-per-subdomain kernel when compiled for the shape, else one
   // block per subdomain when it fits in 256 threads, else a cluster of
   // blocks, else the block kernel with up to 1024 threads; FP64 -> block.
+  // a warm start (u0) is read by the one-warp and block kernels (and the
+  // mapped kernel above); route it to those
+  if (u0) {
+    a.u0 = u0;
+    hz_status ws = HZ_ERR_UNSUPPORTED;
+    if (fp32 && !trial) {
+      ws = launch_choice(pr, a, Choice{kVariantWarp, 1}, fp32, st);
+      if (ws != HZ_OK && ws != HZ_ERR_UNSUPPORTED) return ws;
+    }
+    if (ws == HZ_ERR_UNSUPPORTED) HZ_TRY(launch_choice(pr, a, Choice{kVariantBlock, 0}, fp32, st));
+    if (e1) HZ_CUDA(cudaEventRecord(e1, st));
+    pr.sweeps_launched++;
+    return HZ_OK;
+  }
   const int want = trial ? kVariantBlock : sweep_variant();  // 16-bit trials run on the block kernel
   Choice ch{};
   bool have = false;
@@ -603,9 +618,10 @@ hz_status dots(Ctx& c, const double* V, int64_t ld, int nv, const double* w, boo
 
 // Outer-iteration sweeps keep one sweep of the budget in reserve for the
 // closing sweep of the DD solve (reserve = 1); the closing sweep uses 0.
-hz_status do_sweep(Ctx& c, const double* lam_in, double* lam_out, const double* rhs, double* u_sub, int reserve = 1) {
+hz_status do_sweep(Ctx& c, const double* lam_in, double* lam_out, const double* rhs, double* u_sub, int reserve = 1,
+                   const double* u0 = nullptr) {
   if (c.rep.sweeps + reserve >= c.o.max_sweeps) return fail(HZ_ERR_NOT_CONVERGED, "sweep budget exhausted");
-  HZ_TRY(sweep(c.pr, c.o.precision, c.nt, c.o.wh_iters, c.o.wh_tol, lam_in, lam_out, rhs, u_sub, c.st));
+  HZ_TRY(sweep(c.pr, c.o.precision, c.nt, c.o.wh_iters, c.o.wh_tol, lam_in, lam_out, rhs, u_sub, c.st, u0));
   c.rep.sweeps++;
   return HZ_OK;
 }
@@ -629,7 +645,17 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
   double* tv = pr.tv.as<double>();
   HZ_CUDA(cudaMemsetAsync(xv, 0, vb, c.st));
   // g = T(0): sweep with zero transmission data and the source
-  HZ_TRY(do_sweep(c, xv, gv, rhs, nullptr));
+  // warm start (plain iteration): every sweep's WaveHoltz starts from the
+  // previous sweep's subdomain solutions, carried in uwarm (in place: each
+  // subdomain reads its start at the beginning of the sweep and writes its
+  // result at the end)
+  const bool warm = c.o.wh_warm && c.o.outer == HZ_OUTER_PLAIN;
+  double* uw = nullptr;
+  if (warm) {
+    HZ_TRY(pr.uwarm.ensure((size_t)g.L * g.sub_nodes() * 2 * sizeof(double)));
+    uw = pr.uwarm.as<double>();
+  }
+  HZ_TRY(do_sweep(c, xv, gv, rhs, uw));
   int flags[4];
   double hbuf[8192];
   HZ_TRY(dots(c, gv, 0, 1, gv, real, 0));
@@ -641,7 +667,7 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
       // lambda <- S(lambda) + g, i.e. a sweep with the source (eq. (lambda-iteration))
       HZ_CUDA(cudaMemcpyAsync(xv, gv, vb, cudaMemcpyDeviceToDevice, c.st));
       while (true) {
-        hz_status s = do_sweep(c, xv, tv, rhs, nullptr);
+        hz_status s = do_sweep(c, xv, tv, rhs, uw, 1, uw);
         if (s == HZ_ERR_NOT_CONVERGED) break;
         HZ_TRY(s);
         HZ_TRY(launch_axpby(1.0, tv, -1.0, xv, n2, c.st));  // xv = tv - xv (difference)
@@ -850,7 +876,7 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
   hz_solve_opts relaxed = c.o;
   relaxed.max_sweeps = std::max(c.o.max_sweeps, c.rep.sweeps + 1);  // the closing sweep is always allowed
   Ctx cf{pr, relaxed, c.nt, c.st, c.rep, c.n2};
-  HZ_TRY(do_sweep(cf, xv, tv, rhs, pr.usub.as<double>(), 0));
+  HZ_TRY(do_sweep(cf, xv, tv, rhs, pr.usub.as<double>(), 0, uw));
   HZ_TRY(assemble_add(pr, pr.usub.as<double>(), u, c.st));
   return HZ_OK;
 }
@@ -865,6 +891,8 @@ hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report*
     return fail(HZ_ERR_INVALID_ARG, "invalid solve options");
   if (o.outer < HZ_OUTER_GMRES || o.outer > HZ_OUTER_RGMRES) return fail(HZ_ERR_INVALID_ARG, "unknown outer");
   if (o.gs_passes != 1 && o.gs_passes != 2) return fail(HZ_ERR_INVALID_ARG, "gs_passes must be 1 or 2");
+  if (o.wh_warm != 0 && (o.wh_warm != 1 || o.outer != HZ_OUTER_PLAIN))
+    return fail(HZ_ERR_INVALID_ARG, "wh_warm = 1 needs the plain outer iteration (GMRES needs a fixed linear sweep)");
   hz_solve_report rep{};
   const int nt = o.nt_override > 0 ? o.nt_override : choose_nt(pr, o.cfl);
   rep.nt = nt;
@@ -1262,6 +1290,20 @@ hz_status hz_sweep(hz_problem pr, int32_t precision, int32_t nt, int32_t wh_iter
     HZ_TRY(use_device(*pr));
     return sweep(*pr, precision, nt, wh_iters, wh_tol, lam_in, lam_out, rhs_dev, u_sub,
                  static_cast<cudaStream_t>(stream));
+  });
+}
+
+hz_status hz_sweep_from(hz_problem pr, int32_t precision, int32_t nt, int32_t wh_iters, double wh_tol,
+                        const double* lam_in, double* lam_out, const double* rhs_dev, const double* u0, double* u_sub,
+                        void* stream) {
+  if (!pr || !lam_in || !lam_out || !u0) return fail(HZ_ERR_INVALID_ARG, "null argument");
+  if (lam_in == lam_out) return fail(HZ_ERR_INVALID_ARG, "lam_in and lam_out must not alias");
+  if (precision == HZ_FP16_TRIAL || precision == HZ_BF16_TRIAL)
+    return fail(HZ_ERR_UNSUPPORTED, "warm-started sweeps run in FP32 or FP64");
+  return guard([&]() -> hz_status {
+    HZ_TRY(use_device(*pr));
+    return sweep(*pr, precision, nt, wh_iters, wh_tol, lam_in, lam_out, rhs_dev, u_sub,
+                 static_cast<cudaStream_t>(stream), u0);
   });
 }
 

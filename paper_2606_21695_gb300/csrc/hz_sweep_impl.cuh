@@ -177,7 +177,16 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(const __grid_constant__ Swe
   const Real cpi = Real(a.cpi), spi = Real(a.spi), scale = Real(a.two_over_nt);
   Real ure[RY], uim[RY];
 #pragma unroll
-  for (int r = 0; r < RY; ++r) { ure[r] = Real(0); uim[r] = Real(0); }
+  for (int r = 0; r < RY; ++r) {
+    ure[r] = Real(0);
+    uim[r] = Real(0);
+    const int j = j0 + r;
+    if (a.u0 && active && j < nly) {  // warm start from a previous sweep's subdomain solution
+      const int64_t n = (int64_t)l * nn + (int64_t)j * nlx + i;
+      ure[r] = Real(a.u0[2 * n]);
+      uim[r] = Real(a.u0[2 * n + 1]);
+    }
+  }
   __syncthreads();
 
   __shared__ double red[2 * 32];

@@ -155,6 +155,11 @@ __global__ void __launch_bounds__(kMappedThreads) sweep_mapped_kernel(const __gr
   const Real sigma = Real(a.sigma), omega = Real(a.omega);
   const Real cpi = Real(a.cpi), spi = Real(a.spi), scale = Real(a.two_over_nt);
   Real ure = Real(0), uim = Real(0);
+  if (a.u0 && own) {  // warm start from a previous sweep's subdomain solution
+    const int64_t n = (int64_t)l * nn + t;
+    ure = Real(a.u0[2 * n]);
+    uim = Real(a.u0[2 * n + 1]);
+  }
   __syncthreads();
 
   int m_done = 0;

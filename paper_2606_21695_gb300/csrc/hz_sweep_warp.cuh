@@ -129,6 +129,14 @@ __device__ __forceinline__ void warp_body(const WarpSweepArgs& x, int l, float4 
   float p[NY], pd[NY], vre[NY], vim[NY];
 #pragma unroll
   for (int j = 0; j < NY; ++j) { vre[j] = 0.f; vim[j] = 0.f; }
+  if (a.u0 && live) {  // warm start from a previous sweep's subdomain solution
+#pragma unroll
+    for (int j = 0; j < NY; ++j) {
+      const int64_t n = (int64_t)l * nn + (int64_t)j * nlx + i;
+      vre[j] = (float)a.u0[2 * n];
+      vim[j] = (float)a.u0[2 * n + 1];
+    }
+  }
 
   int m_done = 0;
   for (int m = 0; m < m_wh; ++m) {
