@@ -111,10 +111,27 @@ __global__ void __launch_bounds__(kMappedThreads) sweep_mapped_kernel(const __gr
     en_a = loc - en_b * M;
   }
   __syncthreads();
+  // one element node per thread: its metric, its rows of D (gradient) and its
+  // columns of D (contraction) in registers, its shared-memory addresses fixed
+  Real Dar[M], Dbr[M], Dac[M], Dbc[M];
+  int rowo = 0, colo = 0, f1o = 0, f2o = 0, kown = 0;  // offsets into ps, f1, f2
   if (one_en && own_en) {
     g0 = geo[3 * t];
     g1 = geo[3 * t + 1];
     g2 = geo[3 * t + 2];
+    const int exe = en_e % snx, eye = en_e / snx;
+    rowo = (eye * P + en_b) * nlx + exe * P;
+    colo = (eye * P) * nlx + exe * P + en_a;
+    f1o = en_e * S + en_b * M;
+    f2o = en_e * S + en_a;
+    kown = en_e * S + en_b * M + en_a;
+  }
+#pragma unroll
+  for (int c = 0; c < M; ++c) {
+    Dar[c] = Ds[en_a * M + c];
+    Dbr[c] = Ds[en_b * M + c];
+    Dac[c] = Ds[c * M + en_a];
+    Dbc[c] = Ds[c * M + en_b];
   }
 
   // ---- per-node coefficients and right-hand side (Algorithm 1 step 1)
@@ -176,18 +193,14 @@ __global__ void __launch_bounds__(kMappedThreads) sweep_mapped_kernel(const __gr
       // 2. metric fluxes per element node
       if (one_en) {
         if (own_en) {
-          const int exe = en_e % snx, eye = en_e / snx;
-          const Real* row = ps + (eye * P + en_b) * nlx + exe * P;
-          const Real* col = ps + (eye * P) * nlx + exe * P + en_a;
           Real uxi = Real(0), ueta = Real(0);
 #pragma unroll
           for (int c = 0; c < M; ++c) {
-            uxi += Ds[en_a * M + c] * row[c];
-            ueta += Ds[en_b * M + c] * col[c * nlx];
+            uxi += Dar[c] * ps[rowo + c];
+            ueta += Dbr[c] * ps[colo + c * nlx];
           }
-          const int k = en_e * S + en_b * M + en_a;
-          f1[k] = g0 * uxi + g1 * ueta;
-          f2[k] = g1 * uxi + g2 * ueta;
+          f1[kown] = g0 * uxi + g1 * ueta;
+          f2[kown] = g1 * uxi + g2 * ueta;
         }
       } else {
         for (int en = t; en < Ne; en += blockDim.x) {
@@ -209,6 +222,14 @@ __global__ void __launch_bounds__(kMappedThreads) sweep_mapped_kernel(const __gr
       }
       __syncthreads();
       // 3. element contributions D^T F per element node
+      if (one_en) {
+        if (own_en) {
+          Real acc = Real(0);
+#pragma unroll
+          for (int q = 0; q < M; ++q) acc += Dac[q] * f1[f1o + q] + Dbc[q] * f2[f2o + q * M];
+          cc[kown] = acc;
+        }
+      } else
       for (int en = t; en < Ne; en += blockDim.x) {
         const int e = en / N2, loc = en - e * N2;
         const int b = loc / M, aa = loc - b * M;
