@@ -259,8 +259,9 @@ HZ_API hz_status hz_sweep(hz_problem pr, int32_t precision, int32_t nt, int32_t 
  * opts.wh_warm, Sec. 8): u0 holds subdomain solutions in the u_sub layout
  * (device, complex, L x nly x nlx), typically the previous sweep's; u0 may be
  * the same buffer as u_sub (each subdomain reads its start before it writes
- * its result).  Runs on the one-warp kernel where it fits (FP32), else the
- * block kernel, or the mapped-mesh kernel.  16-bit trial precisions:
+ * its result).  Runs on the register-resident kernels (1, 2 or 4 warps per
+ * subdomain: the autotuned shape) where they fit (FP32), else the block
+ * kernel, or the mapped-mesh kernel.  16-bit trial precisions:
  * HZ_ERR_UNSUPPORTED. */
 HZ_API hz_status hz_sweep_from(hz_problem pr, int32_t precision, int32_t nt, int32_t wh_iters, double wh_tol,
                                const double* lam_in, double* lam_out, const double* rhs, const double* u0,

@@ -460,8 +460,24 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
   if (u0) {
     a.u0 = u0;
     hz_status ws = HZ_ERR_UNSUPPORTED;
-    if (fp32 && !trial) {
-      ws = launch_choice(pr, a, Choice{kVariantWarp, 1}, fp32, st);
+    // the kernel the autotuner chose for this shape when it reads the start
+    // (register-resident 1/2/4 warps or block), HZ_SWEEP_WARPS forcing the
+    // register-resident shape (tests); else one warp, else the block kernel
+    Choice tc{};
+    const bool tuned = pr.autotune && lookup_choice(tune_key(pr.g, precision), &tc) &&
+                       (tc.variant == kVariantWarp || tc.variant == kVariantBlock);
+    const char* hw = std::getenv("HZ_SWEEP_WARPS");
+    if (fp32 && !trial && (hw || (tuned && tc.variant == kVariantWarp) || !tuned)) {
+      const int h = hw ? std::atoi(hw) : (tuned ? tc.ty : 1);
+      ws = launch_choice(pr, a, Choice{kVariantWarp, h}, fp32, st);
+      if (ws != HZ_OK && ws != HZ_ERR_UNSUPPORTED) return ws;
+      if (ws == HZ_ERR_UNSUPPORTED && h != 1) {
+        ws = launch_choice(pr, a, Choice{kVariantWarp, 1}, fp32, st);
+        if (ws != HZ_OK && ws != HZ_ERR_UNSUPPORTED) return ws;
+      }
+    }
+    if (ws == HZ_ERR_UNSUPPORTED && tuned && tc.variant == kVariantBlock) {
+      ws = launch_choice(pr, a, tc, fp32, st);
       if (ws != HZ_OK && ws != HZ_ERR_UNSUPPORTED) return ws;
     }
     if (ws == HZ_ERR_UNSUPPORTED) HZ_TRY(launch_choice(pr, a, Choice{kVariantBlock, 0}, fp32, st));

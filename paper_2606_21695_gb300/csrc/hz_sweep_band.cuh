@@ -34,7 +34,7 @@ struct Shape {
   static constexpr int G = 1;                   // subdomains per block
 };
 
-template <int P, int SY, bool SRC, int H, int B>
+template <int P, int SY, bool SRC, int H, int B, bool WARM>
 __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, int lane, float* xbuf, float4* ecg,
                                           float2* uo, double* red) {
   using S = Shape<P, SY, H>;
@@ -128,6 +128,14 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
   float p[NR], pd[NR], vre[NR], vim[NR];
 #pragma unroll
   for (int r = 0; r < NR; ++r) { vre[r] = 0.f; vim[r] = 0.f; }
+  if (WARM && live) {  // warm start from a previous sweep's subdomain solution (a.u0, this band's rows)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const int64_t n = (int64_t)l * nn + (int64_t)(J0 + r) * nlx + i;
+      vre[r] = (float)a.u0[2 * n];
+      vim[r] = (float)a.u0[2 * n + 1];
+    }
+  }
 
   int m_done = 0;
   // buffer parity runs on across WaveHoltz iterations: consecutive time steps
@@ -298,7 +306,7 @@ __device__ __forceinline__ void band_body(const WarpSweepArgs& x, int l, int g, 
   }
 }
 
-template <int P, int SY, bool SRC, int H>
+template <int P, int SY, bool SRC, int H, bool WARM = false>
 __global__ void __launch_bounds__(H * 32, 7) sweep_band_kernel(const __grid_constant__ WarpSweepArgs x) {
   using S = Shape<P, SY, H>;
   constexpr int NY = S::NY;
@@ -314,10 +322,10 @@ __global__ void __launch_bounds__(H * 32, 7) sweep_band_kernel(const __grid_cons
   float4* ecg = ec_all[g];
   float2* uo = uold_all[w];
   double* red = red_all[g];
-  if (b == 0) band_body<P, SY, SRC, H, 0>(x, l, g, lane, xbuf, ecg, uo, red);
-  else if (b == 1) band_body<P, SY, SRC, H, (H > 1 ? 1 : 0)>(x, l, g, lane, xbuf, ecg, uo, red);
-  else if (b == 2) band_body<P, SY, SRC, H, (H > 2 ? 2 : 0)>(x, l, g, lane, xbuf, ecg, uo, red);
-  else band_body<P, SY, SRC, H, (H > 3 ? 3 : 0)>(x, l, g, lane, xbuf, ecg, uo, red);
+  if (b == 0) band_body<P, SY, SRC, H, 0, WARM>(x, l, g, lane, xbuf, ecg, uo, red);
+  else if (b == 1) band_body<P, SY, SRC, H, (H > 1 ? 1 : 0), WARM>(x, l, g, lane, xbuf, ecg, uo, red);
+  else if (b == 2) band_body<P, SY, SRC, H, (H > 2 ? 2 : 0), WARM>(x, l, g, lane, xbuf, ecg, uo, red);
+  else band_body<P, SY, SRC, H, (H > 3 ? 3 : 0), WARM>(x, l, g, lane, xbuf, ecg, uo, red);
 }
 
 }  // namespace band_sweep

@@ -39,7 +39,9 @@ __host__ __device__ constexpr bool tap(int P, int ne, int j, int t) {
 // tolerance is set (may be null otherwise).
 // RM: the interface boundary mass of a generalised transmission condition may
 // be non-zero (eta != 0); without it the two terms it adds are compiled out.
-template <int P, int SY, bool SRC, bool STASH, bool RM = true>
+// WARM: WaveHoltz starts from a.u0 instead of zero (a separate instantiation,
+// so that the kernels without it compile as before).
+template <int P, int SY, bool SRC, bool STASH, bool RM = true, bool WARM = false>
 __device__ __forceinline__ void warp_body(const WarpSweepArgs& x, int l, float4 (*ec)[2], float2* uo) {
   constexpr int NY = SY * P + 1;
   constexpr int NB = SRC ? NY : 1;  // per-node forcing only when a source is present
@@ -129,7 +131,7 @@ __device__ __forceinline__ void warp_body(const WarpSweepArgs& x, int l, float4 
   float p[NY], pd[NY], vre[NY], vim[NY];
 #pragma unroll
   for (int j = 0; j < NY; ++j) { vre[j] = 0.f; vim[j] = 0.f; }
-  if (a.u0 && live) {  // warm start from a previous sweep's subdomain solution
+  if (WARM && live) {  // warm start from a previous sweep's subdomain solution (a.u0)
 #pragma unroll
     for (int j = 0; j < NY; ++j) {
       const int64_t n = (int64_t)l * nn + (int64_t)j * nlx + i;
@@ -282,14 +284,14 @@ __device__ __forceinline__ void warp_body(const WarpSweepArgs& x, int l, float4 
 
 // One subdomain (one warp) per block: 1024 subdomains spread as 6-7 blocks
 // per SM over 152 SMs, instead of multi-warp blocks landing unevenly.
-template <int P, int SY, bool SRC, bool RM>
+template <int P, int SY, bool SRC, bool RM, bool WARM = false>
 __global__ void __launch_bounds__(32) sweep_warp_kernel(const __grid_constant__ WarpSweepArgs x) {
   constexpr int NY = SY * P + 1;
   __shared__ float4 ec[NY][2];
   __shared__ float2 uo[NY * 32];
   const int l = blockIdx.x;
   if (l >= x.L) return;
-  warp_body<P, SY, SRC, true, RM>(x, l, ec, uo);
+  warp_body<P, SY, SRC, true, RM, WARM>(x, l, ec, uo);
 }
 
 }  // namespace warp_sweep

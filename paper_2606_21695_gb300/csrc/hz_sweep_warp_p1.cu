@@ -12,7 +12,10 @@ hz_status launch(const WarpSweepArgs& a, cudaStream_t st) {
   if constexpr (H == 1) {
     const int blocks = a.L;  // one subdomain (one warp) per block
     const bool rm = a.base.eta != 0.0;  // interface boundary mass present
-    if (a.base.rhs) {
+    if (a.base.u0) {  // warm start (the boundary-mass terms kept: zero when eta = 0)
+      if (a.base.rhs) sweep_warp_kernel<P, SY, true, true, true><<<blocks, 32, 0, st>>>(a);
+      else sweep_warp_kernel<P, SY, false, true, true><<<blocks, 32, 0, st>>>(a);
+    } else if (a.base.rhs) {
       if (rm) sweep_warp_kernel<P, SY, true, true><<<blocks, 32, 0, st>>>(a);
       else sweep_warp_kernel<P, SY, true, false><<<blocks, 32, 0, st>>>(a);
     } else {
@@ -21,7 +24,10 @@ hz_status launch(const WarpSweepArgs& a, cudaStream_t st) {
     }
   } else {
     const int blocks = a.L;  // one subdomain (H warps) per block
-    if (a.base.rhs) band_sweep::sweep_band_kernel<P, SY, true, H><<<blocks, H * 32, 0, st>>>(a);
+    if (a.base.u0) {
+      if (a.base.rhs) band_sweep::sweep_band_kernel<P, SY, true, H, true><<<blocks, H * 32, 0, st>>>(a);
+      else band_sweep::sweep_band_kernel<P, SY, false, H, true><<<blocks, H * 32, 0, st>>>(a);
+    } else if (a.base.rhs) band_sweep::sweep_band_kernel<P, SY, true, H><<<blocks, H * 32, 0, st>>>(a);
     else band_sweep::sweep_band_kernel<P, SY, false, H><<<blocks, H * 32, 0, st>>>(a);
   }
   note_launch();

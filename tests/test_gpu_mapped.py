@@ -231,3 +231,37 @@ def test_mapped_problem_in_batch_and_server_equals_solo(hz):
         hz.hz_server_destroy(srv)
     for c in cases:
         c.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_mapped_full_size_sampled_sweep(hz, precision):
+    """The curved-quadrilateral benchmark workload (cfg2m: 256x256 warped quads,
+    P=3, 32x32 subdomains) at full size: one sweep as the solve launches it,
+    sampled subdomains recomputed by the mapped oracle (each subdomain's cycle
+    depends only on its own data and incoming lambda)."""
+    from paper_2606_21695_gb300.api import Case
+
+    wl = configs.config2m()
+    case = Case(wl)
+    m = sem.Mesh(*wl.box, wl.nx, wl.ny, wl.P, wl.sub_nx, wl.sub_ny)
+    X, Y = wl.node_xy(*m.coords_1d())
+    pr = geom.MappedProblem(m, X, Y, wl.speed_at(X, Y), wl.omega, wl.source_at(X, Y), wl.boundary())
+    nt = hz.hz_problem_nt(case.pr)
+    lam = _rand_lam(pr, 7) * 1e-2
+    prec = hz.HZ_FP64 if precision == "fp64" else hz.HZ_FP32_REFINE
+    got_l, got_u = _run_sweep(hz, case, pr, prec, nt, 3, lam, True)
+    sample = [0, m.Sx - 1, 17 * m.Sx + 9, m.L - m.Sx, m.L - 1, 511]
+    ref_l, ref_u, _ = pr.sweep(lam, pr.rhs(), nt, 3, want_u=True, subset=sample)
+    tol = 1e-11 if precision == "fp64" else 2e-4
+    scale = max(np.max(np.abs(ref_u[sample])), 1e-300)
+    for l in sample:
+        assert np.max(np.abs(got_u[l] - ref_u[l])) < tol * scale, l
+        for e in range(4):
+            r = pr.nbr[l, e]
+            if r >= 0:
+                o = dd.OPPOSITE[e]
+                sl = np.max(np.abs(ref_l[r, o])) + 1e-300
+                assert np.max(np.abs(got_l[r, o] - ref_l[r, o])) < tol * max(sl, np.max(np.abs(lam))), (l, e)
+            else:
+                assert np.all(got_l[l, e] == 0)
+    case.close()

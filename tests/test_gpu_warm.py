@@ -98,6 +98,30 @@ def test_warm_sweep_matches_oracle(hz, nx, ny, sx, sy, P, amp, precision):
     case.close()
 
 
+@pytest.mark.parametrize("warps", ["2", "4"])
+def test_warm_sweep_on_warp_bands(hz, monkeypatch, warps):
+    """The 2- and 4-warp band kernels read the start too (each band its own rows)."""
+    import torch
+
+    monkeypatch.setenv("HZ_SWEEP_WARPS", warps)
+    case, pr = _case(hz, 16, 16, 8, 8, 3)
+    m = pr.mesh
+    nt = hz.hz_problem_nt(case.pr)
+    lam = _lam(pr, 5)
+    rng = np.random.default_rng(6)
+    u0 = rng.standard_normal((m.L, m.nly, m.nlx)) + 1j * rng.standard_normal((m.L, m.nly, m.nlx))
+    ref_l, ref_u, _ = pr.sweep(lam, pr.rhs(), nt, 2, want_u=True, u0=u0)
+    rhs = torch.empty(2 * case.n, dtype=torch.float64, device="cuda")
+    hz.hz_rhs(case.pr, rhs)
+    lout = torch.zeros(2 * hz.hz_lambda_size(case.pr), dtype=torch.float64, device="cuda")
+    ubuf = _dev(u0)
+    hz.hz_sweep_from(case.pr, hz.HZ_FP32_REFINE, nt, 2, 0.0, _dev(lam), lout, rhs, ubuf, ubuf)
+    torch.cuda.synchronize()
+    assert _rel(_host_c(ubuf).reshape(ref_u.shape), ref_u) < 2e-4
+    assert _rel(_host_c(lout).reshape(ref_l.shape), ref_l) < 2e-4
+    case.close()
+
+
 def test_plain_iteration_warm_start_saves_waveholtz_iterations(hz):
     from paper_2606_21695_gb300.api import Case
 
