@@ -35,6 +35,7 @@ if ROOT not in sys.path:
 METRIC = "DOF-updates/s"
 UNIT = "DOF-updates/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
+FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of the part (the FP64 pipe is about 1/64 of the FP32 one)
 # DRAM bytes (read + write) of one launch of the one-warp-per-subdomain sweep
 # on the 256x256, P=3 workload, from one ncu capture of this kernel version
 # (coefficients and lambda read once; independent of the WaveHoltz count)
@@ -178,6 +179,16 @@ def oracle_sample(wl, seconds, nsub_max=1024):
     dof = len(subset) * m.nlx * m.nly * (nt - 1) * m_wh
     desc = f"one sweep (N_t={nt}, {m_wh} WaveHoltz iterations) over {len(subset)} of {m.L} subdomains, FP64 NumPy"
     return dof / el, desc, el
+
+
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json), else
+    the recipe's fallback figure."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
 
 
 def workload(name):
@@ -331,6 +342,40 @@ def run_ours(args):
             fp64 = {"seconds": e0.elapsed_time(e1) * 1e-3, "status": hz.STATUS_NAMES[st64],
                     "sweeps": rep64["sweeps"], "rel_residual": rep64["rel_residual"],
                     "dof_updates_per_s": rep64["dof_updates"] / (e0.elapsed_time(e1) * 1e-3)}
+        # global FP64 residual (HBM-bound): hz_residual on device buffers, L2
+        # flushed before each launch, CUDA events around each call
+        aux = None
+        if world == 1:
+            nres = 20
+            rb = torch.randn(2 * n, dtype=torch.float64, device="cuda")
+            ru = torch.randn(2 * n, dtype=torch.float64, device="cuda")
+            rr = torch.empty_like(rb)
+            rn = torch.zeros(2, dtype=torch.float64, device="cuda")
+            for _ in range(3):
+                hz.hz_residual(case.pr, rb, ru, rr, rn, stream)
+            tot_ms = 0.0
+            for _ in range(nres):
+                flush.fill_(1)
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record()
+                hz.hz_residual(case.pr, rb, ru, rr, rn, stream)
+                a1.record()
+                torch.cuda.synchronize()
+                tot_ms += a0.elapsed_time(a1)
+            res_ms = tot_ms / nres
+            res_bytes = 56 * n  # b, u read (16 B each), c read (8 B), r written (16 B) per node
+            # FP64 work per node: x and y rows of 2P+1 taps on complex u (4(2P+1) FMA), the
+            # weights (4), the H and M terms (4) and b - K u (2); 2 flops per FMA
+            res_flops = 2 * (4 * (2 * P + 1) + 10) * n
+            peak = hbm_peak_gbs()
+            gbs = res_bytes / (res_ms * 1e-3) / 1e9
+            tfl = res_flops / (res_ms * 1e-3) / 1e12
+            aux = {"residual": {"kernel": "residual_kernel + reduce_partials_kernel (FP64, global grid)",
+                                "bound": "fp64 alu", "ms": res_ms, "algorithmic_flops": res_flops,
+                                "achieved_tflops": tfl, "peak_tflops": FP64_PEAK_TFLOPS,
+                                "frac": tfl / FP64_PEAK_TFLOPS, "algorithmic_bytes": res_bytes,
+                                "achieved_gbs": gbs, "hbm_peak_gbs": peak, "hbm_frac": gbs / peak}}
+            del rb, ru, rr, rn
         # 16-bit trials: one sweep each, error against the FP64 sweep (which is
         # checked against the oracle by the test suite)
         trials = None
@@ -388,6 +433,7 @@ def run_ours(args):
                          "avg_launch_ms": avg_launch * 1e3, "launch_share": sweep_s / elapsed},
             "cpu_baseline": cpu,
             "precision_trials": trials,
+            "aux_kernels": aux,
             "e2e": {"value": e2e_dof / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
             "gpu_launches": int(launches),

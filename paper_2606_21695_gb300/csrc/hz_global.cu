@@ -117,48 +117,43 @@ __global__ void rhs_kernel(const __grid_constant__ GlobalArgs a, const double* _
 template <int P>
 __global__ void residual_kernel(const __grid_constant__ GlobalArgs a, const double* __restrict__ b,
                                 const double* __restrict__ u, double* __restrict__ r, double* __restrict__ part) {
+  // the assembled rows in shared memory: the lanes of a warp index them by
+  // their own node class (a per-lane index into parameter space serialises)
+  __shared__ double kx[P + 2][2 * P + 1], ky[P + 2][2 * P + 1];
+  for (int k = threadIdx.y * blockDim.x + threadIdx.x; k < (P + 2) * (2 * P + 1); k += blockDim.x * blockDim.y) {
+    kx[k / (2 * P + 1)][k % (2 * P + 1)] = a.Kx[k / (2 * P + 1)][k % (2 * P + 1)];
+    ky[k / (2 * P + 1)][k % (2 * P + 1)] = a.Ky[k / (2 * P + 1)][k % (2 * P + 1)];
+  }
+  __syncthreads();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   double sums[2] = {0.0, 0.0};
   if (I < a.NXg && J < a.NYg) {
     const int64_t n = (int64_t)J * a.NXg + I;
     const double2* u2 = reinterpret_cast<const double2*>(u);
-    // x row
-    const int ax = I % P, ex = I / P;
-    const bool own_x = ex < a.nx, left_x = (ax == 0) && ex >= 1;
-    double sxr = 0.0, sxi = 0.0;
+    // x and y: assembled rows from the host tables (node class by position
+    // in its element, first and last node of the mesh separately)
+    const int cx = (I == 0) ? P : (I == a.NXg - 1) ? P + 1 : I % P;
+    const int cy = (J == 0) ? P : (J == a.NYg - 1) ? P + 1 : J % P;
+    double sxr = 0.0, sxi = 0.0, syr = 0.0, syi = 0.0;
 #pragma unroll
     for (int tt = -P; tt <= P; ++tt) {
-      double cf = 0.0;
-      const int bb = ax + tt;
-      const bool in_own = own_x && bb >= 0 && bb <= P, in_left = left_x && tt <= 0;
-      if (in_own) cf += a.Kref[ax * (P + 1) + bb];
-      if (in_left) cf += a.Kref[P * (P + 1) + (tt + P)];
-      if (in_own || in_left) {  // structurally inside the mesh
+      if (I + tt >= 0 && I + tt < a.NXg) {  // taps outside the mesh have coefficient 0
         const double2 v = __ldg(&u2[n + tt]);
-        sxr += cf * v.x;
-        sxi += cf * v.y;
+        const double cf = kx[cx][tt + P];
+        sxr = fma(cf, v.x, sxr);
+        sxi = fma(cf, v.y, sxi);
       }
-    }
-    const int ay = J % P, ey = J / P;
-    const bool own_y = ey < a.ny, below_y = (ay == 0) && ey >= 1;
-    double syr = 0.0, syi = 0.0;
-#pragma unroll
-    for (int tt = -P; tt <= P; ++tt) {
-      double cf = 0.0;
-      const int bb = ay + tt;
-      const bool in_own = own_y && bb >= 0 && bb <= P, in_below = below_y && tt <= 0;
-      if (in_own) cf += a.Kref[ay * (P + 1) + bb];
-      if (in_below) cf += a.Kref[P * (P + 1) + (tt + P)];
-      if (in_own || in_below) {
+      if (J + tt >= 0 && J + tt < a.NYg) {
         const double2 v = __ldg(&u2[n + (int64_t)tt * a.NXg]);
-        syr += cf * v.x;
-        syi += cf * v.y;
+        const double cf = ky[cy][tt + P];
+        syr = fma(cf, v.x, syr);
+        syi = fma(cf, v.y, syi);
       }
     }
     const double Wx = a.Wxg[I], Wy = a.Wyg[J];
-    const double Aur = Wy * a.kxs * sxr + Wx * a.kys * syr;
-    const double Aui = Wy * a.kxs * sxi + Wx * a.kys * syi;
+    const double Aur = Wy * sxr + Wx * syr;
+    const double Aui = Wy * sxi + Wx * syi;
     const double c = a.c[n];
     const double M = Wx * Wy / (c * c);
     const double H = (((J == 0 || J == a.NYg - 1) ? Wx : 0.0) + ((I == 0 || I == a.NXg - 1) ? Wy : 0.0)) / c;

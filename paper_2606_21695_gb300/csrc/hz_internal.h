@@ -160,6 +160,12 @@ struct GlobalArgs {
   double omega, kxs, kys, hx2, hy2;
   double Kref[(kMaxP + 1) * (kMaxP + 1)];
   double w[kMaxP + 1];
+  // assembled 1D stiffness rows by node class (class a = node a of an
+  // element, 0 < a < P or a = 0 with elements on both sides; class P: first
+  // node of the mesh; class P+1: last node), taps -P..P, scaled by 2/hx (Kx)
+  // or 2/hy (Ky); built on the host
+  double Kx[kMaxP + 2][2 * kMaxP + 1];
+  double Ky[kMaxP + 2][2 * kMaxP + 1];
   const double* c;
   const double* Wxg;
   const double* Wyg;

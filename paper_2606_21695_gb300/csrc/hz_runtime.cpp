@@ -105,6 +105,21 @@ static GlobalArgs global_args(const Problem& pr) {
   a.hy2 = g.hy / 2.0;
   for (size_t k = 0; k < g.Kref.size(); ++k) a.Kref[k] = g.Kref[k];
   for (int k = 0; k <= g.P; ++k) a.w[k] = g.w[k];
+  // assembled rows: class c < P is an element's node c (c = 0: also node P of
+  // the element to the left); class P the mesh's first node (own element
+  // only), class P+1 its last node (left element only)
+  const int P = g.P;
+  for (int c = 0; c < P + 2; ++c)
+    for (int tt = -P; tt <= P; ++tt) {
+      const int ax = c < P ? c : (c == P ? 0 : P);
+      const bool own = c <= P, left = (c == 0 || c == P + 1);
+      double v = 0.0;
+      const int bb = ax + tt;
+      if (own && bb >= 0 && bb <= P) v += g.Kref[(size_t)ax * (P + 1) + bb];
+      if (left && tt <= 0) v += g.Kref[(size_t)P * (P + 1) + (tt + P)];
+      a.Kx[c][tt + P] = v * a.kxs;
+      a.Ky[c][tt + P] = v * a.kys;
+    }
   a.c = pr.c.as<double>();
   a.Wxg = pr.Wxg.as<double>();
   a.Wyg = pr.Wyg.as<double>();
