@@ -17,6 +17,9 @@
 //   4. per node: A p = the sum of the contributions of its (up to four)
 //      elements (the assembly as a gather: no atomics), then the modified
 //      leapfrog update and the filter sums.
+// For P = 1 and 3 an element's (P+1)^2 nodes fill whole lanes of a warp:
+// steps 2 and 3 are then one step, the contraction reading its element's
+// fluxes by warp shuffles, and a time step has two barriers.
 // Splitting the contraction (3) from the gather (4) keeps the work per thread
 // the same for every node (a cross point gathers four values, not four
 // contractions); element arrays in shared memory use an odd stride per
@@ -61,6 +64,7 @@ struct MappedStride {
 template <typename Real, int P>
 __global__ void __launch_bounds__(kMappedThreads) sweep_mapped_kernel(const __grid_constant__ MappedSweepArgs ma) {
   constexpr int M = P + 1, N2 = M * M, S = MappedStride<P>::value;
+  constexpr bool kWarpElem = (32 % N2) == 0;  // whole elements per warp (P = 1, 3)
   using Tab = typename MTab4<Real>::type;
   const SweepArgs& a = ma.base;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -126,6 +130,7 @@ __global__ void __launch_bounds__(kMappedThreads) sweep_mapped_kernel(const __gr
     f2o = en_e * S + en_a;
     kown = en_e * S + en_b * M + en_a;
   }
+  const int lbase = (t & 31) - (en_b * M + en_a);  // lane of the thread's element node (0, 0)
 #pragma unroll
   for (int c = 0; c < M; ++c) {
     Dar[c] = Ds[en_a * M + c];
@@ -190,8 +195,11 @@ __global__ void __launch_bounds__(kMappedThreads) sweep_mapped_kernel(const __gr
       p += sigma * pd;
       if (own) ps[t] = p;
       __syncthreads();
-      // 2. metric fluxes per element node
-      if (one_en) {
+      if (kWarpElem && one_en) {
+        // 2+3 fused: an element's (P+1)^2 nodes are lanes of one warp, so the
+        // contraction reads the fluxes of its element by shuffles (no
+        // shared-memory round trip, one barrier less per step)
+        Real f1v = Real(0), f2v = Real(0);
         if (own_en) {
           Real uxi = Real(0), ueta = Real(0);
 #pragma unroll
@@ -199,46 +207,66 @@ __global__ void __launch_bounds__(kMappedThreads) sweep_mapped_kernel(const __gr
             uxi += Dar[c] * ps[rowo + c];
             ueta += Dbr[c] * ps[colo + c * nlx];
           }
-          f1[kown] = g0 * uxi + g1 * ueta;
-          f2[kown] = g1 * uxi + g2 * ueta;
+          f1v = g0 * uxi + g1 * ueta;
+          f2v = g1 * uxi + g2 * ueta;
         }
+        Real acc = Real(0);
+#pragma unroll
+        for (int q = 0; q < M; ++q)
+          acc += Dac[q] * __shfl_sync(0xffffffffu, f1v, lbase + en_b * M + q) +
+                 Dbc[q] * __shfl_sync(0xffffffffu, f2v, lbase + q * M + en_a);
+        if (own_en) cc[kown] = acc;
       } else {
+        // 2. metric fluxes per element node
+        if (one_en) {
+          if (own_en) {
+            Real uxi = Real(0), ueta = Real(0);
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+              uxi += Dar[c] * ps[rowo + c];
+              ueta += Dbr[c] * ps[colo + c * nlx];
+            }
+            f1[kown] = g0 * uxi + g1 * ueta;
+            f2[kown] = g1 * uxi + g2 * ueta;
+          }
+        } else {
+          for (int en = t; en < Ne; en += blockDim.x) {
+            const int e = en / N2, loc = en - e * N2;
+            const int b = loc / M, aa = loc - b * M;
+            const int exe = e % snx, eye = e / snx;
+            const Real* row = ps + (eye * P + b) * nlx + exe * P;
+            const Real* col = ps + (eye * P) * nlx + exe * P + aa;
+            Real uxi = Real(0), ueta = Real(0);
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+              uxi += Ds[aa * M + c] * row[c];
+              ueta += Ds[b * M + c] * col[c * nlx];
+            }
+            const Real* g = geo + 3 * en;
+            f1[e * S + loc] = g[0] * uxi + g[1] * ueta;
+            f2[e * S + loc] = g[1] * uxi + g[2] * ueta;
+          }
+        }
+        __syncthreads();
+        // 3. element contributions D^T F per element node
+        if (one_en) {
+          if (own_en) {
+            Real acc = Real(0);
+#pragma unroll
+            for (int q = 0; q < M; ++q) acc += Dac[q] * f1[f1o + q] + Dbc[q] * f2[f2o + q * M];
+            cc[kown] = acc;
+          }
+        } else
         for (int en = t; en < Ne; en += blockDim.x) {
           const int e = en / N2, loc = en - e * N2;
           const int b = loc / M, aa = loc - b * M;
-          const int exe = e % snx, eye = e / snx;
-          const Real* row = ps + (eye * P + b) * nlx + exe * P;
-          const Real* col = ps + (eye * P) * nlx + exe * P + aa;
-          Real uxi = Real(0), ueta = Real(0);
-#pragma unroll
-          for (int c = 0; c < M; ++c) {
-            uxi += Ds[aa * M + c] * row[c];
-            ueta += Ds[b * M + c] * col[c * nlx];
-          }
-          const Real* g = geo + 3 * en;
-          f1[e * S + loc] = g[0] * uxi + g[1] * ueta;
-          f2[e * S + loc] = g[1] * uxi + g[2] * ueta;
-        }
-      }
-      __syncthreads();
-      // 3. element contributions D^T F per element node
-      if (one_en) {
-        if (own_en) {
+          const Real* F1 = f1 + e * S + b * M;  // F1(b, q)
+          const Real* F2 = f2 + e * S + aa;     // F2(q, aa), stride M
           Real acc = Real(0);
 #pragma unroll
-          for (int q = 0; q < M; ++q) acc += Dac[q] * f1[f1o + q] + Dbc[q] * f2[f2o + q * M];
-          cc[kown] = acc;
+          for (int q = 0; q < M; ++q) acc += Ds[q * M + aa] * F1[q] + Ds[q * M + b] * F2[q * M];
+          cc[e * S + loc] = acc;
         }
-      } else
-      for (int en = t; en < Ne; en += blockDim.x) {
-        const int e = en / N2, loc = en - e * N2;
-        const int b = loc / M, aa = loc - b * M;
-        const Real* F1 = f1 + e * S + b * M;  // F1(b, q)
-        const Real* F2 = f2 + e * S + aa;     // F2(q, aa), stride M
-        Real acc = Real(0);
-#pragma unroll
-        for (int q = 0; q < M; ++q) acc += Ds[q * M + aa] * F1[q] + Ds[q * M + b] * F2[q * M];
-        cc[e * S + loc] = acc;
       }
       __syncthreads();
       // 4. gather per node, leapfrog update
