@@ -265,3 +265,46 @@ def test_mapped_full_size_sampled_sweep(hz, precision):
             else:
                 assert np.all(got_l[l, e] == 0)
     case.close()
+
+
+def test_mapped_generalised_transmission_matches_oracle(hz):
+    """Interface condition d_n + k (eta - i zeta) on a mapped mesh: the boundary
+    mass and the zeta-scaled damping use the arc-length edge weights."""
+    from paper_2606_21695_gb300.api import Case, boundary_vector
+
+    wl = _wl(8, 8, 4, 4, 3)
+    case = Case(wl, device=0)
+    hz.hz_problem_set(case.pr, hz.HZ_TRANSMISSION, np.array([0.3, 0.8]))
+    m = sem.Mesh(*wl.box, wl.nx, wl.ny, wl.P, wl.sub_nx, wl.sub_ny)
+    X, Y = wl.node_xy(*m.coords_1d())
+    pr = geom.MappedProblem(m, X, Y, wl.speed_at(X, Y), wl.omega, wl.source_at(X, Y), wl.boundary(),
+                            robin=(0.3, 0.8))
+    nt = pr.choose_nt()
+    lam = _rand_lam(pr, 9)
+    for prec, tol in ((hz.HZ_FP64, 1e-11), (hz.HZ_FP32_REFINE, 2e-4)):
+        got_l, got_u = _run_sweep(hz, case, pr, prec, nt, 2, lam, True)
+        ref_l, ref_u, _ = pr.sweep(lam, pr.rhs(), nt, 2, want_u=True)
+        assert _rel(got_u, ref_u) < tol and _rel(got_l, ref_l) < tol, prec
+    case.close()
+
+
+def test_coordinates_set_from_device_memory(hz):
+    import torch
+
+    from paper_2606_21695_gb300.api import Case
+
+    wl = _wl(8, 8, 4, 4, 2)
+    a = Case(wl)
+    b = Case(configs.Workload(wl.name, wl.box, wl.nx, wl.ny, wl.P, wl.sub_nx, wl.sub_ny, wl.omega, wl.speed_kind,
+                              wl.src_center, wl.src_width, extra={}))
+    xy = torch.from_numpy(np.stack([a.X.ravel(), a.Y.ravel()], 1).ravel().copy()).cuda()
+    hz.hz_problem_set_device(b.pr, hz.HZ_NODE_COORDS, xy, 2 * b.n)
+    hz.hz_problem_set(b.pr, hz.HZ_WAVE_SPEED, a.c.ravel())
+    hz.hz_problem_set(b.pr, hz.HZ_SOURCE, a.f.ravel())
+    o = hz.hz_default_opts(precision=hz.HZ_FP64, tol=1e-10)
+    _, ua, ra = hz.hz_solve(a.pr, o, n=a.n)
+    _, ub, rb = hz.hz_solve(b.pr, o, n=b.n)
+    assert ra["sweep_variant"] == rb["sweep_variant"] == 6
+    assert np.array_equal(ua, ub)
+    a.close()
+    b.close()
