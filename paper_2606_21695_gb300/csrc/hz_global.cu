@@ -377,9 +377,12 @@ __global__ void axpby_kernel(double a, const double* __restrict__ x, double b, d
 }
 
 // y = x / sqrt(n2[0]) (0 if the norm is 0): normalises the next Krylov vector
-// on the device, without a round trip to the host.
-__global__ void scale_inv_norm_kernel(const double* __restrict__ x, const double* __restrict__ n2,
-                                      double* __restrict__ y, int64_t n) {
+// on the device, without a round trip to the host (y may be x).  With flags_src
+// the solve's 4 status words are staged beside the Hessenberg column, so one
+// device-to-host copy carries both.
+__global__ void scale_inv_norm_kernel(const double* x, const double* __restrict__ n2, double* y, int64_t n,
+                                      const int* __restrict__ flags_src, int* __restrict__ flags_dst) {
+  if (flags_src && blockIdx.x == 0 && threadIdx.x < 4) flags_dst[threadIdx.x] = flags_src[threadIdx.x];
   const double v = n2[0];
   const double s = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
@@ -511,8 +514,9 @@ hz_status launch_multi_axpy(const double* V, int64_t ld, int nv, const double* h
   return HZ_OK;
 }
 
-hz_status launch_scale_inv_norm(const double* x, const double* norm2, double* y, int64_t n2, cudaStream_t st) {
-  scale_inv_norm_kernel<<<grid_for(n2, 256), 256, 0, st>>>(x, norm2, y, n2);
+hz_status launch_scale_inv_norm(const double* x, const double* norm2, double* y, int64_t n2, cudaStream_t st,
+                                const int* flags_src, int* flags_dst) {
+  scale_inv_norm_kernel<<<grid_for(n2, 256), 256, 0, st>>>(x, norm2, y, n2, flags_src, flags_dst);
   note_launch();
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;

@@ -236,8 +236,10 @@ hz_status launch_multi_dot(const double* V, int64_t ld, int nv, const double* w,
 int axpy_blocks(int64_t n2);
 hz_status launch_multi_axpy(const double* V, int64_t ld, int nv, const double* h, double* w, int64_t n2,
                             bool real_coef, cudaStream_t st, double* norm_part = nullptr);
-// y = x / sqrt(*norm2) with norm2 in device memory (0 if the norm is 0)
-hz_status launch_scale_inv_norm(const double* x, const double* norm2, double* y, int64_t n2, cudaStream_t st);
+// y = x / sqrt(*norm2) with norm2 in device memory (0 if the norm is 0); y may
+// be x.  With flags_src, also copies 4 status words to flags_dst.
+hz_status launch_scale_inv_norm(const double* x, const double* norm2, double* y, int64_t n2, cudaStream_t st,
+                                const int* flags_src = nullptr, int* flags_dst = nullptr);
 // y = a*x + b*y
 hz_status launch_axpby(double a, const double* x, double b, double* y, int64_t n2, cudaStream_t st);
 

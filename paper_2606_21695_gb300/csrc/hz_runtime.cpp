@@ -744,7 +744,8 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
         // Givens update overlaps the next sweep.  A converged cycle leaves one
         // enqueued step unused.
         const size_t CS = (size_t)4 * m + 8;  // per column: pass-1 dots (m+2), pass-2 dots (m+1), norm: complex
-        HZ_TRY(pr.hcol.ensure((size_t)(m + 1) * CS * sizeof(double)));
+        const size_t CS2 = CS + 2;            // + the 4 status words (16 bytes), read back with the column
+        HZ_TRY(pr.hcol.ensure((size_t)(m + 1) * CS2 * sizeof(double)));
         HZ_TRY(pr.hcol_host.ensure((size_t)(m + 1) * (CS + 4) * sizeof(double)));
         while (pr.gm_events.size() < (size_t)(m + 1)) {
           cudaEvent_t e;
@@ -762,7 +763,7 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
           double* vj = V + (size_t)j * n2;
           double* w = V + (size_t)(j + 1) * n2;
           const int nv = j + 1;
-          double* col = hd + (size_t)j * CS;
+          double* col = hd + (size_t)j * CS2;
           double* nrm = col + 2 * (m + 2) + 2 * (m + 1);
           HZ_TRY(dots_to(c, V, n2, nv, vj, real, col, tv, w));
           if (two_pass) {
@@ -772,10 +773,9 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
           HZ_TRY(launch_multi_axpy(V, n2, nv, two_pass ? col + 2 * (m + 2) : col, w, n2, real, c.st,
                                    pr.part.as<double>()));
           HZ_TRY(launch_reduce_partials(pr.part.as<double>(), axpy_blocks(n2), 2, nrm, c.st));
-          HZ_TRY(launch_scale_inv_norm(w, nrm, w, n2, c.st));
+          HZ_TRY(launch_scale_inv_norm(w, nrm, w, n2, c.st, pr.flags.as<int>(), reinterpret_cast<int*>(col + CS)));
           double* hslot = hh + (size_t)j * (CS + 4);
-          HZ_CUDA(cudaMemcpyAsync(hslot, col, CS * sizeof(double), cudaMemcpyDeviceToHost, c.st));
-          HZ_CUDA(cudaMemcpyAsync(hslot + CS, pr.flags.ptr, 16, cudaMemcpyDeviceToHost, c.st));
+          HZ_CUDA(cudaMemcpyAsync(hslot, col, CS2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
           // while a graph is captured the record must be external to become an
           // event node the host can wait on
           cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
