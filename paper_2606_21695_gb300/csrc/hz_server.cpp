@@ -47,9 +47,14 @@ struct Request {
   std::vector<double> u;
 };
 
-uint64_t estimate_bytes(const Geom& g, const hz_solve_opts& o) {
+uint64_t estimate_bytes(const Geom& g, const hz_solve_opts& o, bool mapped = false) {
   const uint64_t n = (uint64_t)g.n, ns = (uint64_t)g.L * g.sub_nodes(), nl = (uint64_t)g.lam_complex();
   uint64_t b = 0;
+  if (mapped) {  // metric per element node (subdomain FP64 + FP32, global FP64), flux scratch, weights
+    const uint64_t en = (uint64_t)g.nx * g.ny * (g.P + 1) * (g.P + 1);
+    b += en * (24 + 12 + 24 + 32) + ns * 16 + nl * 8 + n * 16;
+  }
+  if (o.wh_warm) b += ns * 16;  // warm-start subdomain solutions
   b += n * 8 + n * 16 + (uint64_t)(2 * g.NXg + 2 * g.NYg) * 16;  // c, f, g
   b += 3 * n * 16;                                                 // b, r, u
   b += ns * 16 + ns * 24;                                          // u_sub, alpha/beta (64 + 32 bit)
@@ -206,7 +211,7 @@ hz_status hz_server_submit(hz_server srv, hz_problem pr, const hz_solve_opts* op
   auto req = std::make_unique<Request>();
   if (opts) req->opts = *opts;
   else hz_default_opts(&req->opts);
-  req->bytes = estimate_bytes(pr->g, req->opts);
+  req->bytes = estimate_bytes(pr->g, req->opts, pr->mapped);
   if (req->bytes > srv->budget) return fail(HZ_ERR_BUSY, "request larger than the server's HBM budget");
   HZ_TRY(clone_problem(*pr, &req->pr));
   req->t_submit = clk::now();
