@@ -305,7 +305,9 @@ HZ_API hz_status hz_residual(hz_problem pr, const double* b, const double* u, do
  * return HZ_ERR_UNSUPPORTED before anything is launched.  The first call on a
  * device looks up that array's device address (set-up): make it before any
  * stream capture.  All calls share the array, so calls that overlap on the
- * GPU race; serialise them on one stream. */
+ * GPU race; serialise them on one stream.  The mesh is the Cartesian grid of
+ * hz_mesh_create (node coordinates set on a problem with HZ_NODE_COORDS are
+ * not seen here; use hz_residual on that problem). */
 HZ_API hz_status hz_residual_noalloc(hz_mesh mesh, double omega, const double* c, const double* b, const double* u,
                                      double* r, double* norms2, void* stream);
 
