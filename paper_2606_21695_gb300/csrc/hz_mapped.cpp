@@ -234,28 +234,4 @@ hz_status set_node_coords(Problem& pr, const double* xy) {
   return HZ_OK;
 }
 
-hz_status copy_mapped(const Problem& src, Problem& dst) {
-  dst.mapped = src.mapped;
-  dst.mapped_mu = src.mapped_mu;
-  dst.mapped_D = src.mapped_D;
-  if (!src.mapped) return HZ_OK;
-  auto copy = [](DevBuf& d, const DevBuf& s) -> hz_status {
-    if (!s.ptr) return HZ_OK;
-    HZ_TRY(d.ensure(s.bytes));
-    HZ_CUDA(cudaMemcpy(d.ptr, s.ptr, s.bytes, cudaMemcpyDeviceToDevice));
-    return HZ_OK;
-  };
-  HZ_TRY(copy(dst.mgeo64, src.mgeo64));
-  HZ_TRY(copy(dst.mgeo32, src.mgeo32));
-  HZ_TRY(copy(dst.mWs, src.mWs));
-  HZ_TRY(copy(dst.mEs, src.mEs));
-  HZ_TRY(copy(dst.mshare, src.mshare));
-  HZ_TRY(copy(dst.mgeog, src.mgeog));
-  HZ_TRY(copy(dst.mWg, src.mWg));
-  HZ_TRY(copy(dst.mHw, src.mHw));
-  HZ_TRY(copy(dst.mbw, src.mbw));
-  HZ_TRY(dst.mflux.ensure(src.mflux.bytes));
-  return HZ_OK;
-}
-
 }  // namespace hz

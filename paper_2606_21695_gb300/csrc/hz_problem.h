@@ -87,7 +87,7 @@ int choose_nt(const Problem& pr, double cfl);
 hz_status prepare(Problem& pr, int nt, cudaStream_t st);
 hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, const double* lam_in, double* lam_out,
                 const double* rhs, double* u_sub, cudaStream_t st,
-                const double* u0 = nullptr);
+                const double* u0 = nullptr, const int* rect = nullptr);
 hz_status residual(Problem& pr, const double* b, const double* u, double* r, double* norms2_dev, cudaStream_t st);
 hz_status rhs(Problem& pr, double* b, cudaStream_t st);
 hz_status assemble_add(Problem& pr, const double* u_sub, double* u, cudaStream_t st);
@@ -96,7 +96,6 @@ hz_status check_ready(const Problem& pr);
 // Geometry of a mapped mesh from 2n node coordinates (x, y interleaved):
 // validates J > 0 at every GLL node and uploads the metric and weights.
 hz_status set_node_coords(Problem& pr, const double* xy);
-hz_status copy_mapped(const Problem& src, Problem& dst);
 void release_step_graphs(Problem& pr);
 bool is_default_stream(cudaStream_t s);
 unsigned long long launch_count();

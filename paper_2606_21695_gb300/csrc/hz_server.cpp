@@ -1,14 +1,16 @@
 // Request server: continuous batching of Helmholtz solves on one device.
 //
-// submit() snapshots the problem (device-to-device copies of its fields) and
-// queues it.  A pool of worker threads admits queued requests in arrival
-// order whenever the request's estimated device footprint fits in the HBM
-// budget; each admitted solve runs on its own CUDA stream, and with
-// opts.pack the sweeps of all admitted solves go out together, one packed
-// launch per outer step (hz_pack.cpp), so a request that arrives while others
-// run is admitted as soon as a worker and memory free up and joins the next
-// packed launch.  Latency is
-// measured from submit() to the completed device-to-host copy of u.
+// submit() snapshots the problem's fields into host memory and queues the
+// request; nothing of a queued request lives on the device.  A pool of worker
+// threads admits queued requests whenever a request's estimated device
+// footprint fits in the HBM budget (first fit in arrival order; a request
+// passed over too often blocks the ones behind it until it fits, so large
+// requests are not starved), and only then copies its fields to the device.
+// Each admitted solve runs on its own CUDA stream, and with opts.pack the
+// sweeps of all admitted solves go out together, one packed launch per outer
+// step (hz_pack.cpp), so a request that arrives while others run is admitted
+// as soon as a worker and memory free up and joins the next packed launch.
+// Latency is measured from submit() to the completed device-to-host copy of u.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,9 +35,26 @@ namespace {
 
 using clk = std::chrono::steady_clock;
 
+// Device buffers of a problem that carry its fields (the rest is solver
+// workspace, sized by the solve itself).
+using BufMember = DevBuf hz_problem_s::*;
+constexpr BufMember kFieldBufs[] = {&hz_problem_s::c,      &hz_problem_s::f,      &hz_problem_s::gb,
+                                    &hz_problem_s::Wxg,    &hz_problem_s::Wyg,    &hz_problem_s::wxs,
+                                    &hz_problem_s::wys,    &hz_problem_s::mgeo64, &hz_problem_s::mgeo32,
+                                    &hz_problem_s::mWs,    &hz_problem_s::mEs,    &hz_problem_s::mshare,
+                                    &hz_problem_s::mgeog,  &hz_problem_s::mWg,    &hz_problem_s::mHw,
+                                    &hz_problem_s::mbw};
+constexpr int kNumFieldBufs = (int)(sizeof(kFieldBufs) / sizeof(kFieldBufs[0]));
+// A request passed over this many times by first-fit admission blocks the
+// queue behind it until it fits.
+constexpr int kMaxPassOver = 64;
+
 struct Request {
   uint64_t ticket = 0;
-  std::unique_ptr<hz_problem_s> pr;
+  std::unique_ptr<hz_problem_s> pr;  // scalars from submit; device buffers only once admitted
+  std::vector<std::vector<unsigned char>> host;  // field snapshot, one per kFieldBufs entry
+  size_t flux_bytes = 0;             // mapped meshes: residual flux scratch to allocate
+  int passed_over = 0;
   hz_solve_opts opts{};
   uint64_t bytes = 0;
   clk::time_point t_submit;
@@ -63,7 +82,9 @@ uint64_t estimate_bytes(const Geom& g, const hz_solve_opts& o, bool mapped = fal
   return b;
 }
 
-hz_status clone_problem(const hz_problem_s& src, std::unique_ptr<hz_problem_s>* out) {
+// Host snapshot of a problem: its scalars and a copy of every field buffer.
+// Queued requests hold no device memory.
+hz_status snapshot_problem(const hz_problem_s& src, Request* req) {
   auto pr = std::make_unique<hz_problem_s>();
   pr->g = src.g;
   pr->device = src.device;
@@ -73,23 +94,41 @@ hz_status clone_problem(const hz_problem_s& src, std::unique_ptr<hz_problem_s>* 
   pr->robin_zeta = src.robin_zeta;
   pr->has_c = src.has_c;
   pr->has_omega = src.has_omega;
+  pr->mapped = src.mapped;
+  pr->mapped_mu = src.mapped_mu;
+  pr->mapped_D = src.mapped_D;
   HZ_CUDA(cudaSetDevice(src.device));
-  auto copy = [](DevBuf& dst, const DevBuf& s) -> hz_status {
-    if (!s.ptr) return HZ_OK;
-    HZ_TRY(dst.ensure(s.bytes));
-    HZ_CUDA(cudaMemcpy(dst.ptr, s.ptr, s.bytes, cudaMemcpyDeviceToDevice));
-    return HZ_OK;
-  };
-  HZ_TRY(copy(pr->c, src.c));
-  HZ_TRY(copy(pr->f, src.f));
-  HZ_TRY(copy(pr->gb, src.gb));
-  HZ_TRY(copy(pr->Wxg, src.Wxg));
-  HZ_TRY(copy(pr->Wyg, src.Wyg));
-  HZ_TRY(copy(pr->wxs, src.wxs));
-  HZ_TRY(copy(pr->wys, src.wys));
-  HZ_TRY(copy_mapped(src, *pr));
-  HZ_CUDA(cudaStreamCreateWithFlags(&pr->stream, cudaStreamNonBlocking));
-  *out = std::move(pr);
+  req->host.assign(kNumFieldBufs, {});
+  for (int k = 0; k < kNumFieldBufs; ++k) {
+    const DevBuf& b = src.*kFieldBufs[k];
+    if (!b.ptr) continue;
+    try {
+      req->host[k].resize(b.bytes);
+    } catch (...) {
+      return fail(HZ_ERR_OOM, "host snapshot of the problem failed");
+    }
+    HZ_CUDA(cudaMemcpy(req->host[k].data(), b.ptr, b.bytes, cudaMemcpyDeviceToHost));
+  }
+  req->flux_bytes = src.mapped ? src.mflux.bytes : 0;
+  req->pr = std::move(pr);
+  return HZ_OK;
+}
+
+// Copies an admitted request's fields to the device and gives it a stream;
+// the host snapshot is dropped.
+hz_status materialize(Request* req) {
+  hz_problem_s& pr = *req->pr;
+  HZ_CUDA(cudaSetDevice(pr.device));
+  for (int k = 0; k < kNumFieldBufs; ++k) {
+    std::vector<unsigned char>& h = req->host[k];
+    if (h.empty()) continue;
+    DevBuf& d = pr.*kFieldBufs[k];
+    HZ_TRY(d.ensure(h.size()));
+    HZ_CUDA(cudaMemcpy(d.ptr, h.data(), h.size(), cudaMemcpyHostToDevice));
+    std::vector<unsigned char>().swap(h);
+  }
+  if (req->flux_bytes) HZ_TRY(pr.mflux.ensure(req->flux_bytes));
+  HZ_CUDA(cudaStreamCreateWithFlags(&pr.stream, cudaStreamNonBlocking));
   return HZ_OK;
 }
 
@@ -111,6 +150,22 @@ struct hz_server_s {
   std::unique_ptr<Packer> packer;  // sweeps of concurrently served solves, one launch per step
   clk::time_point t_start = clk::now();
 
+  // First queued request that fits in the budget (removed from the queue), or
+  // null.  Requests ahead of it that do not fit count one more pass-over; one
+  // that reached kMaxPassOver stops the scan, so it is admitted next.
+  Request* pick() {
+    for (auto it = queue.begin(); it != queue.end(); ++it) {
+      Request* r = *it;
+      if (in_use + r->bytes <= budget) {
+        for (auto jt = queue.begin(); jt != it; ++jt) (*jt)->passed_over++;
+        queue.erase(it);
+        return r;
+      }
+      if (r->passed_over >= kMaxPassOver) return nullptr;
+    }
+    return nullptr;
+  }
+
   void worker_loop() {
     cudaSetDevice(device);
     std::unique_lock<std::mutex> lk(mu);
@@ -118,17 +173,18 @@ struct hz_server_s {
       Request* job = nullptr;
       cv_work.wait(lk, [&] {
         if (stopping) return true;
-        return !queue.empty() && in_use + queue.front()->bytes <= budget;
+        job = pick();
+        return job != nullptr;
       });
       if (stopping) return;
-      job = queue.front();
-      queue.pop_front();
       in_use += job->bytes;
       lk.unlock();
+      // copy the fields to the device now that the budget holds them, then
       // run the solve on the request's own stream
       hz_problem_s& pr = *job->pr;
       const size_t nb = (size_t)pr.g.n * 2 * sizeof(double);
-      hz_status s = pr.uvec.ensure(nb);
+      hz_status s = materialize(job);
+      if (s == HZ_OK) s = pr.uvec.ensure(nb);
       hz_solve_report rep{};
       const bool packed = job->opts.pack && packer && Packer::packable(pr, job->opts);
       if (packed) {
@@ -213,7 +269,7 @@ hz_status hz_server_submit(hz_server srv, hz_problem pr, const hz_solve_opts* op
   else hz_default_opts(&req->opts);
   req->bytes = estimate_bytes(pr->g, req->opts, pr->mapped);
   if (req->bytes > srv->budget) return fail(HZ_ERR_BUSY, "request larger than the server's HBM budget");
-  HZ_TRY(clone_problem(*pr, &req->pr));
+  HZ_TRY(snapshot_problem(*pr, req.get()));
   req->t_submit = clk::now();
   std::lock_guard<std::mutex> lk(srv->mu);
   if (srv->stopping) return fail(HZ_ERR_BUSY, "server is shutting down");

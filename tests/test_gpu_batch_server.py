@@ -127,3 +127,42 @@ def test_server_admission_refuses_over_budget_without_disturbing_others(hz):
         assert done1 and st1 == hz.HZ_OK
     finally:
         hz.hz_server_destroy(srv)
+
+
+def test_server_queued_requests_hold_no_device_memory(hz):
+    """A burst larger than the HBM budget: queued requests are host
+    snapshots, so the device memory the server holds stays within the budget
+    it admits against (plus the per-solve allocations the estimate covers
+    loosely), and the admitted bytes never exceed the budget.  The solves are
+    cut short (40 sweeps): only their memory matters here."""
+    import torch
+
+    from paper_2606_21695_gb300.api import Case
+
+    big = Case(configs.scaled(configs.config2(), 128, 128, 8, 8, name="burst"))  # 148k nodes, 256 subdomains
+    opts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=1e-8, max_sweeps=40)
+    ok = (hz.HZ_OK, hz.HZ_ERR_NOT_CONVERGED)
+    srv = hz.hz_server_create(0, 96 << 20)  # about two such solves at a time
+    try:
+        # one request first, so module loading and the first solve's tuning are not counted
+        done, st, _, _ = hz.hz_server_poll(srv, hz.hz_server_submit(srv, big.pr, opts), -1, n=big.n)
+        assert done and st in ok
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        n_req = 48  # their fields alone (c, f: 24 bytes per node) would be ~170 MB on the device
+        tickets = [hz.hz_server_submit(srv, big.pr, opts) for _ in range(n_req)]
+        peak = 0
+        for _ in range(40):
+            free, _ = torch.cuda.mem_get_info()
+            peak = max(peak, free0 - free)
+            assert hz.hz_server_stats(srv)["hbm_in_use"] <= 96 << 20
+            time.sleep(0.01)
+        print("burst: device bytes held above the idle level", peak)
+        assert peak <= (96 << 20) + (64 << 20)
+        for t in tickets:
+            done, st, _, _ = hz.hz_server_poll(srv, t, -1, n=big.n)
+            assert done and st in ok
+        assert hz.hz_server_stats(srv)["hbm_in_use"] == 0
+    finally:
+        hz.hz_server_destroy(srv)
+        big.close()
