@@ -176,6 +176,9 @@ extern "C" hz_status hz_residual_noalloc(hz_mesh mesh, double omega, const doubl
     return fail(HZ_ERR_UNSUPPORTED, "mesh too large for hz_residual_noalloc: at most " +
                                         std::to_string((long long)kNoallocMaxBlocks) +
                                         " blocks of 32 x 8 nodes (about 33.5 M nodes)");
+  if (grd.y > 65535u)  // the launch's y dimension: thin meshes with many node rows
+    return fail(HZ_ERR_UNSUPPORTED, "mesh too large for hz_residual_noalloc: at most 65535 blocks of 8 node rows "
+                                    "(524280 node rows)");
   double* part = nullptr;
   HZ_TRY(scratch_for_current_device(&part));
   NoallocArgs a{};
