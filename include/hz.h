@@ -173,6 +173,17 @@ HZ_API hz_status hz_last_error(char* buf, size_t n);
  * (all devices, all threads).  Not part of the method; for accounting. */
 HZ_API hz_status hz_kernel_launches(uint64_t* count);
 
+/* Measured FMA-pipe rate of the current device (a measurement utility; the
+ * paper has no counterpart).  Runs a kernel of independent fused
+ * multiply-adds only -- FP32 for precision HZ_FP32_REFINE, FP64 for HZ_FP64 --
+ * on 4 blocks of 256 threads per SM, each thread iters x 128 FMAs, timed with
+ * CUDA events on a private stream after one shorter warm-up launch.  Writes
+ * the achieved TFLOP/s (2 flops per FMA) and the timed launch's milliseconds.
+ * This is the denominator the sweep kernels' roofline fractions are quoted
+ * against.  Errors: HZ_ERR_INVALID_ARG for another precision, iters < 1 or a
+ * null pointer; HZ_ERR_CUDA if the launch fails. */
+HZ_API hz_status hz_fma_peak(int32_t precision, int32_t iters, double* tflops, double* ms);
+
 /* ------------------------------------------------------------------ mesh --
  * Structured mesh of [x0,x1] x [y0,y1] with nx x ny quad elements of degree
  * P (1..7), split into subdomains of sub_nx x sub_ny elements (Sec. 3, Fig. 1;
@@ -267,6 +278,38 @@ HZ_API hz_status hz_sweep_from(hz_problem pr, int32_t precision, int32_t nt, int
                                const double* lam_in, double* lam_out, const double* rhs, const double* u0,
                                double* u_sub, void* stream);
 
+/* Rank-local sweep for a problem split over several GPUs (Sec. 8: the DD
+ * sweep partitions by subdomains and only interface data crosses between
+ * GPUs).  Sweeps only the subdomains of the rectangle of subdomain columns
+ * sx0 .. sx0+sw-1 and rows sy0 .. sy0+sh-1 (subdomain l = sy * S_x + sx),
+ * with the arithmetic of hz_sweep, one launch.  lam_in, lam_out, rhs and
+ * u_sub keep the whole problem's layouts (as hz_sweep).  Writes in lam_out:
+ * the slots the rectangle's subdomains send to every neighbour -- inside the
+ * rectangle, and the slots of neighbouring subdomains outside it (the cut
+ * interfaces, to be sent to their owner: hz_lambda_gather) -- and zero in
+ * its own outer-boundary slots; slots of its own subdomains that face
+ * subdomains outside the rectangle are not written (their owner's sweep
+ * produces them: hz_lambda_scatter).  u_sub (or NULL): solutions of the
+ * rectangle's subdomains only.  Over a partition of the subdomain grid into
+ * rectangles, the union of the rank-local sweeps plus the exchange gives
+ * bitwise the lambda of one hz_sweep.  HZ_ERR_INVALID_ARG for a rectangle
+ * outside the grid. */
+HZ_API hz_status hz_sweep_rect(hz_problem pr, int32_t precision, int32_t nt, int32_t wh_iters, double wh_tol,
+                               int32_t sx0, int32_t sy0, int32_t sw, int32_t sh, const double* lam_in,
+                               double* lam_out, const double* rhs, double* u_sub, void* stream);
+
+/* Packing of cut-interface transmission data for the exchange between GPUs
+ * (Sec. 8).  slots: device array of count pairs (l, e) (int32: subdomain,
+ * edge 0..3 = W, E, S, N) of a lambda vector; buf: device array of count x NE
+ * complex values, slot k at buf[k NE .. (k+1) NE - 1].  gather copies the
+ * slots of lam into buf (the send buffer); scatter copies buf into the slots
+ * of lam (after the receive).  The slot lists of a sender and its receiver
+ * must enumerate the same interfaces in the same order. */
+HZ_API hz_status hz_lambda_gather(hz_problem pr, const int32_t* slots, int32_t count, const double* lam, double* buf,
+                                  void* stream);
+HZ_API hz_status hz_lambda_scatter(hz_problem pr, const int32_t* slots, int32_t count, const double* buf, double* lam,
+                                   void* stream);
+
 /* The same sweep for count problems in one packed launch (the batched form
  * used by hz_solve_batch and the server; Algorithm 1, Sec. 6): every
  * subdomain of every problem is swept by one warp, FP32, with nts[k] time
@@ -301,8 +344,9 @@ HZ_API hz_status hz_residual(hz_problem pr, const double* b, const double* u, do
  * current device; mesh is the host-side mesh description.  Block partial
  * sums live in a fixed array in the library's device memory (2 MiB, held by
  * every device that loads the library until the process exits), which limits
- * the mesh to 2^17 blocks of 32 x 8 nodes (about 33.5 M nodes); larger meshes
- * return HZ_ERR_UNSUPPORTED before anything is launched.  The first call on a
+ * the mesh to 2^17 blocks of 32 x 8 nodes (about 33.5 M nodes) and at most
+ * 524280 node rows (65535 blocks of 8 rows); larger meshes return
+ * HZ_ERR_UNSUPPORTED before anything is launched.  The first call on a
  * device looks up that array's device address (set-up): make it before any
  * stream capture.  All calls share the array, so calls that overlap on the
  * GPU race; serialise them on one stream.  The mesh is the Cartesian grid of

@@ -73,6 +73,7 @@ def load():
         "hz_default_opts": (None, [C.POINTER(hz_solve_opts)]),
         "hz_last_error": (i32, [C.c_char_p, C.c_size_t]),
         "hz_kernel_launches": (i32, [C.POINTER(u64)]),
+        "hz_fma_peak": (i32, [i32, i32, dp, dp]),
         "hz_mesh_create": (i32, [d, d, d, d, i32, i32, i32, i32, i32, C.POINTER(vp)]),
         "hz_mesh_num_nodes": (i32, [vp, C.POINTER(i64)]),
         "hz_mesh_node_coords": (i32, [vp, dp]),
@@ -90,6 +91,9 @@ def load():
         "hz_prepare": (i32, [vp, i32, vp]),
         "hz_sweep": (i32, [vp, i32, i32, i32, d, vp, vp, vp, vp, vp]),
         "hz_sweep_from": (i32, [vp, i32, i32, i32, d, vp, vp, vp, vp, vp, vp]),
+        "hz_sweep_rect": (i32, [vp, i32, i32, i32, d, i32, i32, i32, i32, vp, vp, vp, vp, vp]),
+        "hz_lambda_gather": (i32, [vp, vp, i32, vp, vp, vp]),
+        "hz_lambda_scatter": (i32, [vp, vp, i32, vp, vp, vp]),
         "hz_sweep_packed": (i32, [C.POINTER(vp), i32, C.POINTER(i32), i32, C.POINTER(vp), C.POINTER(vp),
                                   C.POINTER(vp), C.POINTER(vp), vp]),
         "hz_rhs": (i32, [vp, vp, vp]),
@@ -115,8 +119,9 @@ def exported_names():
     return ["hz_default_opts", "hz_last_error", "hz_kernel_launches", "hz_mesh_create", "hz_mesh_num_nodes", "hz_mesh_node_coords",
             "hz_mesh_destroy", "hz_problem_create", "hz_problem_set", "hz_problem_set_device", "hz_problem_destroy",
             "hz_problem_nt", "hz_solve", "hz_solve_device", "hz_solve_batch", "hz_lambda_size", "hz_prepare", "hz_sweep", "hz_sweep_from",
+            "hz_sweep_rect", "hz_lambda_gather", "hz_lambda_scatter",
             "hz_sweep_packed", "hz_rhs",
-            "hz_residual", "hz_residual_noalloc", "hz_assemble_add", "hz_server_create", "hz_server_submit", "hz_server_poll",
+            "hz_residual", "hz_residual_noalloc", "hz_fma_peak", "hz_assemble_add", "hz_server_create", "hz_server_submit", "hz_server_poll",
             "hz_server_stats", "hz_server_destroy"]
 
 
@@ -124,6 +129,13 @@ def hz_last_error():
     buf = C.create_string_buffer(1024)
     load().hz_last_error(buf, len(buf))
     return buf.value.decode(errors="replace")
+
+
+def hz_fma_peak(precision, iters):
+    """Measured FMA rate of the current device: (TFLOP/s, ms of the timed launch)."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(load().hz_fma_peak(precision, iters, C.byref(tf), C.byref(ms)))
+    return tf.value, ms.value
 
 
 def hz_kernel_launches():
@@ -288,6 +300,23 @@ def hz_sweep(pr, precision, nt, wh_iters, wh_tol, lam_in, lam_out, rhs=None, u_s
 def hz_sweep_from(pr, precision, nt, wh_iters, wh_tol, lam_in, lam_out, rhs, u0, u_sub=None, stream=None):
     _check(load().hz_sweep_from(pr, precision, nt, wh_iters, wh_tol, _ptr(lam_in), _ptr(lam_out), _ptr(rhs), _ptr(u0),
                                 _ptr(u_sub), _stream(stream)))
+
+
+def hz_sweep_rect(pr, precision, nt, wh_iters, wh_tol, rect, lam_in, lam_out, rhs=None, u_sub=None, stream=None):
+    """Rank-local sweep of the subdomain rectangle rect = (sx0, sy0, sw, sh)."""
+    sx0, sy0, sw, sh = (int(v) for v in rect)
+    _check(load().hz_sweep_rect(pr, precision, nt, wh_iters, wh_tol, sx0, sy0, sw, sh, _ptr(lam_in), _ptr(lam_out),
+                                _ptr(rhs), _ptr(u_sub), _stream(stream)))
+
+
+def hz_lambda_gather(pr, slots, count, lam, buf, stream=None):
+    """buf[k] = lambda slot slots[k] = (l, e) (device int32 pairs)."""
+    _check(load().hz_lambda_gather(pr, _ptr(slots), int(count), _ptr(lam), _ptr(buf), _stream(stream)))
+
+
+def hz_lambda_scatter(pr, slots, count, buf, lam, stream=None):
+    """lambda slot slots[k] = (l, e) = buf[k]."""
+    _check(load().hz_lambda_scatter(pr, _ptr(slots), int(count), _ptr(buf), _ptr(lam), _stream(stream)))
 
 
 def hz_sweep_packed(problems, nts, wh_iters, lam_in, lam_out, rhs=None, u_sub=None, stream=None):

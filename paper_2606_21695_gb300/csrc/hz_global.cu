@@ -5,6 +5,8 @@
 // fixed summation order (deterministic results).
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <cmath>
 
 #include "hz_internal.h"
@@ -391,7 +393,8 @@ __global__ void scale_inv_norm_kernel(const double* x, const double* __restrict_
 
 int grid_for(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
-  if (g > 152 * 8) g = 152 * 8;
+  const int64_t cap = (int64_t)sm_count() * 8;  // 8 resident blocks of 256 threads per SM
+  if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;
 }
@@ -458,10 +461,28 @@ hz_status launch_assemble_add(const AssembleArgs& a, const double* u_sub, double
   return HZ_OK;
 }
 
+int sm_count() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];  // 0 = not looked up yet
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    (void)cudaGetLastError();
+    return 1;  // grid-stride kernels stay correct with any grid
+  }
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+    (void)cudaGetLastError();
+    v = 1;
+  }
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
 // blocks for multi_dot: 2 per SM, chunks of at most 4096 complex entries (64 KB of shared memory)
 int vec_blocks(int64_t n2) {
   const int64_t nc = n2 / 2;
-  int64_t nb = 2 * 152;
+  int64_t nb = 2 * (int64_t)sm_count();
   if ((nc + nb - 1) / nb > 4096) nb = (nc + 4095) / 4096;
   if (nb > nc) nb = nc > 0 ? nc : 1;
   return (int)nb;
@@ -517,6 +538,29 @@ hz_status launch_multi_axpy(const double* V, int64_t ld, int nv, const double* h
 hz_status launch_scale_inv_norm(const double* x, const double* norm2, double* y, int64_t n2, cudaStream_t st,
                                 const int* flags_src, int* flags_dst) {
   scale_inv_norm_kernel<<<grid_for(n2, 256), 256, 0, st>>>(x, norm2, y, n2, flags_src, flags_dst);
+  note_launch();
+  HZ_CUDA(cudaGetLastError());
+  return HZ_OK;
+}
+
+// One thread per complex entry of the listed slots; slot k occupies entries
+// [k NE, (k+1) NE) of the packed buffer.
+__global__ void lambda_slots_kernel(const int32_t* __restrict__ slots, int count, int NE, const double2* src,
+                                    double2* dst, int gather) {
+  const int64_t total = (int64_t)count * NE;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(q / NE), t = (int)(q % NE);
+    const int64_t slot = ((int64_t)slots[2 * k] * 4 + slots[2 * k + 1]) * NE + t;
+    if (gather) dst[q] = src[slot];
+    else dst[slot] = src[q];
+  }
+}
+
+hz_status launch_lambda_slots(const int32_t* slots, int count, int NE, const double* src, double* dst, bool gather,
+                              cudaStream_t st) {
+  const int64_t total = (int64_t)count * NE;
+  lambda_slots_kernel<<<grid_for(total, 256), 256, 0, st>>>(slots, count, NE, reinterpret_cast<const double2*>(src),
+                                                             reinterpret_cast<double2*>(dst), gather ? 1 : 0);
   note_launch();
   HZ_CUDA(cudaGetLastError());
   return HZ_OK;

@@ -91,7 +91,18 @@ struct SweepArgs {
   unsigned long long* wh_iter_sum;  // sum over subdomains of WaveHoltz iterations
   int* flags;           // bit 0: non-finite value seen
   const double* u0;     // [L][nly][nlx] complex or null: WaveHoltz starts from it instead of zero
+  // rank-local sweeps (hz_sweep_rect): with rect_w > 0 the launch covers the
+  // rect_w x (count / rect_w) subdomains of the grid starting at subdomain
+  // column rect_x0, row rect_y0; every array keeps the whole problem's layout
+  int rect_x0, rect_y0, rect_w, rect_h;
 };
+
+// Subdomains one launch sweeps: the rectangle's, or all L.
+inline int sweep_count(const SweepArgs& a, int L) { return a.rect_w > 0 ? a.rect_w * a.rect_h : L; }
+// Subdomain swept by the k-th block (or cluster, or warp group) of a launch.
+__host__ __device__ __forceinline__ int sweep_subdomain(const SweepArgs& a, int k) {
+  return a.rect_w > 0 ? (a.rect_y0 + k / a.rect_w) * a.Sx + a.rect_x0 + k % a.rect_w : k;
+}
 
 // Parameters of the warp-per-subdomain FP32 sweep (subdomains <= 32 node
 // columns).  The assembled y-stiffness rows divided by the row weight are
@@ -228,6 +239,8 @@ int residual_mapped_blocks(const MappedGlobalArgs& a);
 // writes x to w_out (the Arnoldi vector (I - S) v from v and S v; w_out must
 // not overlap V_0..V_{nv-1} or w).
 int vec_blocks(int64_t n2);
+// Streaming multiprocessors of the current device (looked up once per device).
+int sm_count();
 hz_status launch_multi_dot(const double* V, int64_t ld, int nv, const double* w, const double* w_sub, double* w_out,
                            int64_t n2, bool real_dot, double* part, int nblocks, cudaStream_t st);
 // w -= sum_k h[k] V_k  (h complex on device, nv entries).  With norm_part
@@ -240,6 +253,11 @@ hz_status launch_multi_axpy(const double* V, int64_t ld, int nv, const double* h
 // be x.  With flags_src, also copies 4 status words to flags_dst.
 hz_status launch_scale_inv_norm(const double* x, const double* norm2, double* y, int64_t n2, cudaStream_t st,
                                 const int* flags_src = nullptr, int* flags_dst = nullptr);
+// Transmission-data slots (l, e) listed in slots (2 int32 per slot, device):
+// gather = true copies lam slot k (NE complex) to buf[k], else buf[k] to the
+// lam slot.
+hz_status launch_lambda_slots(const int32_t* slots, int count, int NE, const double* src, double* dst, bool gather,
+                              cudaStream_t st);
 // y = a*x + b*y
 hz_status launch_axpby(double a, const double* x, double b, double* y, int64_t n2, cudaStream_t st);
 

@@ -262,28 +262,29 @@ void store_choice(const std::string& key, Choice c) {
 
 hz_status launch_choice(Problem& pr, const SweepArgs& a0, Choice c, bool fp32, cudaStream_t st) {
   const Geom& g = pr.g;
+  const int count = sweep_count(a0, g.L);
   hz_status s = HZ_ERR_UNSUPPORTED;
   if (c.variant == kVariantWarp) {
     if (!fp32) return HZ_ERR_UNSUPPORTED;
     WarpSweepArgs w{};
     w.base = a0;
-    w.L = g.L;
+    w.L = count;
     warp_rows(g, &w);
     s = launch_sweep_warp(g.P, g.sny, c.ty > 0 ? c.ty : 1, w, st);
   } else if (c.variant == kVariantClusterBand) {
     if (!fp32) return HZ_ERR_UNSUPPORTED;
     SweepArgs a = a0;
     a.ty_force = c.ty;  // 8: 8 rows per warp band, else 16
-    s = launch_sweep_cband(g.P, a, g.L, st);
+    s = launch_sweep_cband(g.P, a, count, st);
   } else if (c.variant == kVariantCluster) {
     if (!fp32) return HZ_ERR_UNSUPPORTED;
     SweepArgs a = a0;
     a.ty_force = c.ty;  // 4: 4P rows per thread, else 2P
-    s = launch_sweep_cluster(g.P, a, g.L, st);
+    s = launch_sweep_cluster(g.P, a, count, st);
   } else {
     SweepArgs a = a0;
     a.ty_force = c.ty;
-    s = launch_sweep(fp32, g.P, a, g.L, st);
+    s = launch_sweep(fp32, g.P, a, count, st);
   }
   if (s == HZ_OK) {
     pr.last_variant = c.variant;
@@ -405,7 +406,7 @@ hz_status autotune(Problem& pr, int precision, int nt, int m_wh, cudaStream_t st
 }
 
 hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, const double* lam_in, double* lam_out,
-                const double* rhs, double* u_sub, cudaStream_t st, const double* u0) {
+                const double* rhs, double* u_sub, cudaStream_t st, const double* u0, const int* rect) {
   HZ_TRY(prepare(pr, nt, st));
   HZ_TRY(ensure_flags(pr));
   const Geom& g = pr.g;
@@ -414,6 +415,13 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
   const bool trial = precision == HZ_FP16_TRIAL || precision == HZ_BF16_TRIAL;
   const bool fp32 = precision != HZ_FP64;
   SweepArgs a = make_sweep_args(pr, fp32, nt, m_wh, wh_tol, lam_in, lam_out, rhs, u_sub);
+  if (rect) {  // rank-local sweep of a rectangle of subdomains
+    a.rect_x0 = rect[0];
+    a.rect_y0 = rect[1];
+    a.rect_w = rect[2];
+    a.rect_h = rect[3];
+  }
+  const int count = sweep_count(a, g.L);
   if (trial) a.round_mode = precision == HZ_FP16_TRIAL ? 1 : 2;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (pr.time_sweeps) {
@@ -441,7 +449,7 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
     ma.snx = g.snx;
     ma.sny = g.sny;
     for (size_t k = 0; k < pr.mapped_D.size(); ++k) ma.D[k] = pr.mapped_D[k];
-    HZ_TRY(launch_sweep_mapped(fp32, g.P, ma, g.L, st));
+    HZ_TRY(launch_sweep_mapped(fp32, g.P, ma, count, st));
     pr.last_variant = kVariantMapped;
     pr.last_shape = 0;
     if (e1) HZ_CUDA(cudaEventRecord(e1, st));
@@ -450,7 +458,7 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
   }
   // A solve running as a member of a packer hands its sweep over: one packed
   // launch per outer step covers the subdomains of every member.
-  if (pr.packer && precision == HZ_FP32_REFINE && !(wh_tol > 0.0) && !u0) {
+  if (pr.packer && precision == HZ_FP32_REFINE && !(wh_tol > 0.0) && !u0 && !rect) {
     const int shape = packed_shape_id(g.P, g.sny, g.nlx);
     if (shape >= 0) {
       WarpSweepArgs w{};
@@ -1335,6 +1343,42 @@ hz_status hz_sweep_from(hz_problem pr, int32_t precision, int32_t nt, int32_t wh
     HZ_TRY(use_device(*pr));
     return sweep(*pr, precision, nt, wh_iters, wh_tol, lam_in, lam_out, rhs_dev, u_sub,
                  static_cast<cudaStream_t>(stream), u0);
+  });
+}
+
+hz_status hz_sweep_rect(hz_problem pr, int32_t precision, int32_t nt, int32_t wh_iters, double wh_tol, int32_t sx0,
+                        int32_t sy0, int32_t sw, int32_t sh, const double* lam_in, double* lam_out, const double* rhs_dev,
+                        double* u_sub, void* stream) {
+  if (!pr || !lam_in || !lam_out) return fail(HZ_ERR_INVALID_ARG, "null argument");
+  if (lam_in == lam_out) return fail(HZ_ERR_INVALID_ARG, "lam_in and lam_out must not alias");
+  const Geom& g = pr->g;
+  if (sw < 1 || sh < 1 || sx0 < 0 || sy0 < 0 || sx0 + sw > g.Sx || sy0 + sh > g.Sy)
+    return fail(HZ_ERR_INVALID_ARG, "subdomain rectangle outside the subdomain grid");
+  return guard([&]() -> hz_status {
+    HZ_TRY(use_device(*pr));
+    const int rect[4] = {sx0, sy0, sw, sh};
+    return sweep(*pr, precision, nt, wh_iters, wh_tol, lam_in, lam_out, rhs_dev, u_sub,
+                 static_cast<cudaStream_t>(stream), nullptr, rect);
+  });
+}
+
+hz_status hz_lambda_gather(hz_problem pr, const int32_t* slots, int32_t count, const double* lam, double* buf,
+                           void* stream) {
+  if (!pr || count < 0 || (count > 0 && (!slots || !lam || !buf))) return fail(HZ_ERR_INVALID_ARG, "null argument");
+  if (count == 0) return HZ_OK;
+  return guard([&]() -> hz_status {
+    HZ_TRY(use_device(*pr));
+    return launch_lambda_slots(slots, count, pr->g.NE, lam, buf, /*gather=*/true, static_cast<cudaStream_t>(stream));
+  });
+}
+
+hz_status hz_lambda_scatter(hz_problem pr, const int32_t* slots, int32_t count, const double* buf, double* lam,
+                            void* stream) {
+  if (!pr || count < 0 || (count > 0 && (!slots || !lam || !buf))) return fail(HZ_ERR_INVALID_ARG, "null argument");
+  if (count == 0) return HZ_OK;
+  return guard([&]() -> hz_status {
+    HZ_TRY(use_device(*pr));
+    return launch_lambda_slots(slots, count, pr->g.NE, buf, lam, /*gather=*/false, static_cast<cudaStream_t>(stream));
   });
 }
 

@@ -316,8 +316,9 @@ __global__ void __launch_bounds__(H * 32, 7) sweep_band_kernel(const __grid_cons
   __shared__ double red_all[S::G][2 * H];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = w / H, b = w % H;
-  const int l = blockIdx.x * S::G + g;
-  if (l >= x.L) return;  // the whole group leaves together (all H warps share l)
+  const int k = blockIdx.x * S::G + g;
+  if (k >= x.L) return;  // the whole group leaves together (all H warps share l)
+  const int l = sweep_subdomain(x.base, k);
   float* xbuf = xbuf_all[g];
   float4* ecg = ec_all[g];
   float2* uo = uold_all[w];

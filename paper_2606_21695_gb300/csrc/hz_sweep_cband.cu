@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(Shape<P, SY, RB>::W * 32) sweep_cband_kernel(c
   cg::cluster_group cluster = cg::this_cluster();
   const int q = (int)cluster.block_rank();
   const int CN = (int)cluster.num_blocks();
-  const int l = blockIdx.x / CN;  // the whole cluster shares one subdomain
+  const int l = sweep_subdomain(a, blockIdx.x / CN);  // the whole cluster shares one subdomain
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // zero the halos (read before any neighbour writes at the domain edges)
   {

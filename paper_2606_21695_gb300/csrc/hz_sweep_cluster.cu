@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_k
   float* sm = reinterpret_cast<float*>(smem_raw);
 
   const int q = (int)cluster.block_rank();
-  const int l = blockIdx.x / CN;
+  const int l = sweep_subdomain(a, blockIdx.x / CN);
   const int sxi = l % a.Sx, syi = l / a.Sx;
   const int nlx = a.nlx, nly = a.nly;
   const int i0 = q * BW;

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(const __grid_constant__ Swe
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* sm = reinterpret_cast<Real*>(smem_raw);
 
-  const int l = blockIdx.x;
+  const int l = sweep_subdomain(a, blockIdx.x);
   const int sxi = l % a.Sx, syi = l / a.Sx;
   const int nlx = a.nlx, nly = a.nly;
   const int t = threadIdx.x;

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kMappedThreads) sweep_mapped_kernel(const __gr
   __shared__ double red[2 * 32];
   __shared__ int stop_flag;
 
-  const int l = blockIdx.x, t = threadIdx.x;
+  const int l = sweep_subdomain(ma.base, blockIdx.x), t = threadIdx.x;
   const int sxi = l % a.Sx, syi = l / a.Sx;
   for (int k = t; k < N2; k += blockDim.x) Ds[k] = Real(ma.D[k]);
   {

@@ -289,8 +289,8 @@ __global__ void __launch_bounds__(32) sweep_warp_kernel(const __grid_constant__ 
   constexpr int NY = SY * P + 1;
   __shared__ float4 ec[NY][2];
   __shared__ float2 uo[NY * 32];
-  const int l = blockIdx.x;
-  if (l >= x.L) return;
+  if ((int)blockIdx.x >= x.L) return;
+  const int l = sweep_subdomain(x.base, blockIdx.x);
   warp_body<P, SY, SRC, true, RM, WARM>(x, l, ec, uo);
 }
 
