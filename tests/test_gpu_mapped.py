@@ -2,8 +2,8 @@
 the oracle's mapped discretisation (oracle/geom.py, pinned on the CPU).
 
 Tolerances as in test_gpu_parity.py: FP64 sweep 1e-11 relative (both sides
-use the element form; summation orders differ), FP32 sweep 2e-4 (eps_32 N_t
-m_wh growth with margin), solutions against the direct solve 1e-7 after a
+use the element form; summation orders differ), FP32 sweep FP32_REL = 2e-5
+(tests/_tolerances.py), solutions against the direct solve 1e-7 after a
 1e-11 residual (cond(K) times the residual on these small meshes).
 """
 
@@ -12,6 +12,9 @@ import pytest
 
 from oracle import dd, geom, sem
 from workloads import configs
+
+import _tolerances as _tol
+from _tolerances import FP32_REL
 
 pytestmark = pytest.mark.gpu
 
@@ -63,7 +66,7 @@ def _host_c(t):
 
 
 def _rel(a, b):
-    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+    return _tol.record(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
 def _run_sweep(hz, case, pr, precision, nt, m_wh, lam, with_rhs):
@@ -116,8 +119,8 @@ def test_mapped_sweep_fp32_error(hz, nx, ny, sx, sy, P):
     lam = _rand_lam(pr, 2)
     got_l, got_u = _run_sweep(hz, case, pr, hz.HZ_FP32_REFINE, nt, 2, lam, True)
     ref_l, ref_u, _ = pr.sweep(lam, pr.rhs(), nt, 2, want_u=True)
-    assert _rel(got_u, ref_u) < 2e-4
-    assert _rel(got_l, ref_l) < 2e-4
+    assert _rel(got_u, ref_u) < FP32_REL
+    assert _rel(got_l, ref_l) < FP32_REL
     case.close()
 
 
@@ -252,7 +255,7 @@ def test_mapped_full_size_sampled_sweep(hz, precision):
     got_l, got_u = _run_sweep(hz, case, pr, prec, nt, 3, lam, True)
     sample = [0, m.Sx - 1, 17 * m.Sx + 9, m.L - m.Sx, m.L - 1, 511]
     ref_l, ref_u, _ = pr.sweep(lam, pr.rhs(), nt, 3, want_u=True, subset=sample)
-    tol = 1e-11 if precision == "fp64" else 2e-4
+    tol = 1e-11 if precision == "fp64" else FP32_REL
     scale = max(np.max(np.abs(ref_u[sample])), 1e-300)
     for l in sample:
         assert np.max(np.abs(got_u[l] - ref_u[l])) < tol * scale, l
@@ -281,7 +284,7 @@ def test_mapped_generalised_transmission_matches_oracle(hz):
                             robin=(0.3, 0.8))
     nt = pr.choose_nt()
     lam = _rand_lam(pr, 9)
-    for prec, tol in ((hz.HZ_FP64, 1e-11), (hz.HZ_FP32_REFINE, 2e-4)):
+    for prec, tol in ((hz.HZ_FP64, 1e-11), (hz.HZ_FP32_REFINE, FP32_REL)):
         got_l, got_u = _run_sweep(hz, case, pr, prec, nt, 2, lam, True)
         ref_l, ref_u, _ = pr.sweep(lam, pr.rhs(), nt, 2, want_u=True)
         assert _rel(got_u, ref_u) < tol and _rel(got_l, ref_l) < tol, prec

@@ -2,14 +2,17 @@
 meshes, degrees, frequencies and N_t) against the FP64 oracle, and against
 the single-problem register-resident kernel it shares its body with.
 
-Tolerance for FP32 against the oracle: 2e-4 relative, derived in
-test_gpu_parity.py (eps_32 x N_t x m_wh with a margin of ~8)."""
+Tolerance for FP32 against the oracle: FP32_REL = 2e-5 relative, derived in
+tests/_tolerances.py."""
 
 import numpy as np
 import pytest
 
 from oracle import dd, sem
 from workloads import configs
+
+import _tolerances as _tol
+from _tolerances import FP32_REL
 
 pytestmark = pytest.mark.gpu
 
@@ -63,7 +66,7 @@ def _host(t):
 
 
 def _rel(a, b):
-    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+    return _tol.record(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
 def _buffers(hz, case, pr, lam, with_rhs):
@@ -116,8 +119,8 @@ def test_packed_sweep_matches_oracle(hz, members):
     for (case, pr, lam, nt), (gl, gu), r in zip(members, got, with_rhs):
         ref_l, ref_u, _ = pr.sweep(lam, pr.rhs() if r else None, nt, wh, want_u=True)
         assert np.all(np.isfinite(gl))
-        assert _rel(gu, ref_u) < 2e-4, pr.mesh.P
-        assert _rel(gl, ref_l) < 2e-4, pr.mesh.P
+        assert _rel(gu, ref_u) < FP32_REL, pr.mesh.P
+        assert _rel(gl, ref_l) < FP32_REL, pr.mesh.P
 
 
 def test_packed_result_does_not_depend_on_the_mix(hz, members):
@@ -184,5 +187,5 @@ def test_packed_sweep_with_generalised_transmission(hz):
     lam = _lam(pr, 77)
     (gl, gu), = _packed(hz, [(case, pr, lam, nt)], 3, [True])
     ref_l, ref_u, _ = pr.sweep(lam, pr.rhs(), nt, 3, want_u=True)
-    assert _rel(gu, ref_u) < 2e-4 and _rel(gl, ref_l) < 2e-4
+    assert _rel(gu, ref_u) < FP32_REL and _rel(gl, ref_l) < FP32_REL
     case.close()

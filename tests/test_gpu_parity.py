@@ -6,11 +6,9 @@ Tolerances:
 * FP64 kernels vs oracle: 1e-12 relative to the largest entry (same
   arithmetic, different summation order: the kernel uses the assembled
   tensor-product stiffness, the oracle the element-by-element form).
-* FP32 sweep vs FP64 oracle: 2e-4 relative.  Derivation: the WaveHoltz loop
-  runs (N_t - 1) m_wh leapfrog steps; each step adds O(eps_32 = 6e-8)
-  relative rounding to p and p-dot, and the filter sum accumulates N_t terms,
-  so the error grows like eps_32 * N_t * m_wh ~ 6e-8 * 80 * 5 = 2.4e-5; the
-  bound keeps a factor of ~8 margin.
+* FP32 sweep vs FP64 oracle: FP32_REL = 2e-5 relative; the derivation (FP32
+  rounding of the leapfrog state accumulating over the (N_t - 1) m_wh steps of
+  a sweep) and the measured errors it is set against are in tests/_tolerances.py.
 * solutions: the solve stops on the global FP64 residual; the error against
   the direct solve is bounded by cond(K) * residual, checked at 1e-10 with a
   1e-12 residual target on these small meshes.
@@ -23,6 +21,9 @@ import pytest
 
 from oracle import dd, sem
 from workloads import configs
+
+import _tolerances as _tol
+from _tolerances import FP32_REL
 
 pytestmark = pytest.mark.gpu
 
@@ -82,7 +83,7 @@ def _host_c(t):
 
 
 def _rel(a, b):
-    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+    return _tol.record(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
 def _run_sweep(hz, case, pr, precision, nt, m_wh, lam, with_rhs, wh_tol=0.0):
@@ -178,7 +179,7 @@ def test_sweep_fp32_within_bound(hz, sweep_variant, nx, ny, sx, sy, P):
         ref_l, ref_u, _ = pr.sweep(lam, pr.rhs() if with_rhs else None, nt, 5, want_u=True)
         eu, el = _rel(got_u, ref_u), _rel(got_l, ref_l)
         print(f"fp32 sweep [{sweep_variant}] rhs={with_rhs} rel err u {eu:.2e} lambda {el:.2e} (Nt={nt})")
-        assert eu < 2e-4 and el < 2e-4
+        assert eu < FP32_REL and el < FP32_REL
 
 
 @pytest.mark.parametrize("variant,env,layout", [
@@ -199,10 +200,11 @@ def test_sweep_fp32_generalised_transmission_all_kernels(hz, monkeypatch, varian
     case, pr = _pair(hz, wl, g_seed=nx + P, robin=robin)
     nt = hz.hz_problem_nt(case.pr)
     lam = _rand_lam(pr, 12)
+    bound = _tol.fp32_bound(sx * P + 1)
     for with_rhs in (True, False):
         got_l, got_u = _run_sweep(hz, case, pr, hz.HZ_FP32_REFINE, nt, 3, lam, with_rhs)
         ref_l, ref_u, _ = pr.sweep(lam, pr.rhs() if with_rhs else None, nt, 3, want_u=True)
-        assert _rel(got_u, ref_u) < 2e-4 and _rel(got_l, ref_l) < 2e-4, variant
+        assert _rel(got_u, ref_u) < bound and _rel(got_l, ref_l) < bound, variant
     case.close()
 
 
@@ -229,7 +231,7 @@ def test_fp32_warp_variant_covers_benchmark_shape(hz, monkeypatch):
     nt = hz.hz_problem_nt(case.pr)
     lam = _rand_lam(pr, 5)
     got_l, _ = _run_sweep(hz, case, pr, hz.HZ_FP32_REFINE, nt, 3, lam, False)
-    assert _rel(got_l, pr.sweep(lam, None, nt, 3)) < 2e-4
+    assert _rel(got_l, pr.sweep(lam, None, nt, 3)) < FP32_REL
     wl2 = _wl(6, 6, 3, 3, 3)  # sub_ny = 3: no warp instantiation
     case2, pr2 = _pair(hz, wl2)
     with pytest.raises(hz.HzError) as e:
@@ -405,7 +407,7 @@ def test_config2_full_size_sampled_sweep(hz, precision):
     m = pr.mesh
     sample = [0, m.Sx - 1, 17 * m.Sx + 9, m.L - m.Sx, m.L - 1, 511]
     ref_l, ref_u, _ = pr.sweep(lam, pr.rhs(), nt, 5, want_u=True, subset=sample)
-    tol = 1e-12 if precision == "fp64" else 2e-4
+    tol = 1e-12 if precision == "fp64" else FP32_REL
     scale = max(np.max(np.abs(ref_u[sample])), 1e-300)
     for l in sample:
         assert np.max(np.abs(got_u[l] - ref_u[l])) < tol * scale, l
@@ -440,10 +442,11 @@ def test_sweep_fp32_cluster_matches_oracle(hz, monkeypatch, nx, ny, sx, sy, P, t
     case, pr = _pair(hz, wl, g_seed=nx + P)
     nt = hz.hz_problem_nt(case.pr)
     lam = _rand_lam(pr, 6)
+    bound = _tol.fp32_bound(sx * P + 1)
     for with_rhs in (True, False):
         got_l, got_u = _run_sweep(hz, case, pr, hz.HZ_FP32_REFINE, nt, 4, lam, with_rhs)
         ref_l, ref_u, _ = pr.sweep(lam, pr.rhs() if with_rhs else None, nt, 4, want_u=True)
-        assert _rel(got_u, ref_u) < 2e-4 and _rel(got_l, ref_l) < 2e-4
+        assert _rel(got_u, ref_u) < bound and _rel(got_l, ref_l) < bound
     # tolerance mode: the stopping decision is taken identically by every CTA
     g1, u1 = _run_sweep(hz, case, pr, hz.HZ_FP32_REFINE, nt, 40, lam, True, wh_tol=1e-4)
     _, ref4, _ = pr.sweep(lam, pr.rhs(), nt, 40, wh_tol=1e-4, want_u=True)
@@ -471,11 +474,12 @@ def test_sweep_fp32_cluster_bands_match_oracle(hz, monkeypatch, nx, ny, sx, sy, 
     case, pr = _pair(hz, wl, g_seed=nx + 3 * P)
     nt = hz.hz_problem_nt(case.pr)
     lam = _rand_lam(pr, 8)
+    bound = _tol.fp32_bound(sx * P + 1)
     for with_rhs in (True, False):
         got_l, got_u = _run_sweep(hz, case, pr, hz.HZ_FP32_REFINE, nt, 3, lam, with_rhs)
         ref_l, ref_u, _ = pr.sweep(lam, pr.rhs() if with_rhs else None, nt, 3, want_u=True)
         assert np.all(np.isfinite(got_l))
-        assert _rel(got_u, ref_u) < 2e-4 and _rel(got_l, ref_l) < 2e-4
+        assert _rel(got_u, ref_u) < bound and _rel(got_l, ref_l) < bound
 
 
 @pytest.mark.parametrize("variant", ["cband", "cluster"])
@@ -494,27 +498,31 @@ def test_config3_full_size_sampled_sweep(hz, monkeypatch, variant):
     sample = [0, m.L - 1, 16 * m.Sx + 16]
     ref_l, ref_u, _ = pr.sweep(lam, pr.rhs(), nt, 3, want_u=True, subset=sample)
     scale = np.max(np.abs(ref_u[sample]))
+    bound = _tol.FP32_REL_WIDE  # 129 node columns
     for l in sample:
-        assert np.max(np.abs(got_u[l] - ref_u[l])) < 2e-4 * scale, l
+        assert _tol.record(np.max(np.abs(got_u[l] - ref_u[l])) / scale) < bound, l
         for e in range(4):
             r = pr.nbr[l, e]
             if r >= 0:
                 o = dd.OPPOSITE[e]
                 s_ = max(np.max(np.abs(ref_l[r, o])), np.max(np.abs(lam)))
-                assert np.max(np.abs(got_l[r, o] - ref_l[r, o])) < 2e-4 * s_, (l, e)
+                assert _tol.record(np.max(np.abs(got_l[r, o] - ref_l[r, o])) / s_) < bound, (l, e)
     case.close()
 
 
 def test_config1_full_solve_matches_direct(hz):
-    """32x32 quads, P = 2, 4x4 subdomains, FP64 throughout, to 1e-10."""
+    """32x32 quads, P = 2, 4x4 subdomains, FP64 throughout: the solution
+    agrees with the oracle's sparse direct solve to 1e-10 relative (L2), the
+    FP64 path's target; the solve runs to a 1e-12 residual so that
+    cond(K) x residual stays below it."""
     wl = configs.config1()
     case, pr = _pair(hz, wl)
-    opts = hz.hz_default_opts(tol=1e-10, inner_tol=1e-8)
+    opts = hz.hz_default_opts(tol=1e-12, inner_tol=1e-10)
     st, u, rep = hz.hz_solve(case.pr, opts, n=case.n)
     ud = pr.direct_solve().ravel()
-    err = np.linalg.norm(u - ud) / np.linalg.norm(ud)
+    err = _tol.record(np.linalg.norm(u - ud) / np.linalg.norm(ud), "L2 vs direct")
     print("cfg1 fp64", rep, "err", err)
-    assert st == hz.HZ_OK and rep["rel_residual"] <= 1e-10 and err < 1e-8
+    assert st == hz.HZ_OK and rep["rel_residual"] <= 1e-12 and err < 1e-10
 
 
 @pytest.mark.parametrize("trial", ["fp16", "bf16"])
