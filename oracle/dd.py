@@ -50,7 +50,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from . import krylov
-from .sem import Mesh, stiffness_apply, stiffness_matrix
+from .sem import Mesh, nested_dissection_order, stiffness_apply, stiffness_matrix
 
 EDGE_W, EDGE_E, EDGE_S, EDGE_N = 0, 1, 2, 3
 OPPOSITE = {EDGE_W: EDGE_E, EDGE_E: EDGE_W, EDGE_S: EDGE_N, EDGE_N: EDGE_S}
@@ -112,9 +112,23 @@ class Problem:
         w = self.omega
         return (A - 1j * w * sp.diags(self.Hdiag.ravel()) - w * w * sp.diags(self.Mdiag.ravel())).tocsc()
 
-    def direct_solve(self, b=None):
+    def direct_solve(self, b=None, ordering="default"):
+        """K^{-1} b by a sparse LU.  ordering="nd": the matrix is permuted by
+        nested dissection of the node grid first (sem.nested_dissection_order)
+        and factorised in that order with diagonal pivots (the same LU, with
+        far less fill on meshes of 10^5 nodes)."""
         b = self.rhs() if b is None else b
-        return spla.spsolve(self.matrix(), b.ravel()).reshape(b.shape)
+        if ordering != "nd":
+            return spla.spsolve(self.matrix(), b.ravel()).reshape(b.shape)
+        m = self.mesh
+        perm = nested_dissection_order(m.NX, m.NY, m.P)
+        K = self.matrix()
+        lu = spla.splu(K[perm][:, perm].tocsc(), permc_spec="NATURAL", diag_pivot_thresh=0.0,
+                       options=dict(SymmetricMode=True))
+        up = lu.solve(b.ravel()[perm])
+        u = np.empty_like(up)
+        u[perm] = up
+        return u.reshape(b.shape)
 
     # -------------------------------------------------------- subdomains --
     def _sub_setup(self):

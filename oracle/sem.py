@@ -202,3 +202,44 @@ def stiffness_matrix(P, D, w, hx, hy, nex, ney):
     n = nX * (ney * P + 1)
     A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
     return A.tocsr()
+
+
+def nested_dissection_order(NX, NY, P, leaf=256):
+    """Fill-reducing elimination order of the NX x NY node grid (x fastest)
+    for a sparse direct solve: recursive bisection by node lines.  A node row
+    or column on an element boundary separates the nodes on its two sides
+    (they share no element, so the stiffness couples them only through it);
+    each half is ordered first, the separator last.  Blocks of at most `leaf`
+    nodes keep their natural order.  Returns a permutation of range(NX NY).
+    Used only to make the oracle's direct solves of the larger test meshes
+    affordable (the factorisation is the same LU)."""
+    out = []
+
+    def natural(i0, i1, j0, j1):
+        out.extend(J * NX + I for J in range(j0, j1) for I in range(i0, i1))
+
+    def rec(i0, i1, j0, j1):
+        w, h = i1 - i0, j1 - j0
+        if w * h <= leaf:
+            natural(i0, i1, j0, j1)
+            return
+        if w >= h:
+            s = i0 + ((w // 2) // P) * P  # an element-boundary column
+            if s <= i0 or s >= i1 - 1:
+                natural(i0, i1, j0, j1)
+                return
+            rec(i0, s, j0, j1)
+            rec(s + 1, i1, j0, j1)
+            out.extend(J * NX + s for J in range(j0, j1))
+        else:
+            s = j0 + ((h // 2) // P) * P
+            if s <= j0 or s >= j1 - 1:
+                natural(i0, i1, j0, j1)
+                return
+            rec(i0, i1, j0, s)
+            rec(i0, i1, s + 1, j1)
+            out.extend(s * NX + I for I in range(i0, i1))
+
+    rec(0, NX, 0, NY)
+    return np.asarray(out)
+

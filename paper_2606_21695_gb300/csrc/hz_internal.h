@@ -132,6 +132,9 @@ hz_status launch_sweep_packed(const WarpSweepArgs* descs, const int* offsets, in
 // exchange through distributed shared memory).  HZ_ERR_UNSUPPORTED when no
 // cluster shape fits.
 hz_status launch_sweep_cluster(int P, const SweepArgs& a, int L, cudaStream_t st);
+// The same cluster sweep in FP64 (the plain-FP64 path for subdomains too
+// large for one block).
+hz_status launch_sweep_cluster_f64(int P, const SweepArgs& a, int L, cudaStream_t st);
 
 // FP32 sweep of subdomains wider than 32 node columns by a cluster of CTAs,
 // one per 32-column band, one warp per row band, state in registers (degree

@@ -277,10 +277,10 @@ hz_status launch_choice(Problem& pr, const SweepArgs& a0, Choice c, bool fp32, c
     a.ty_force = c.ty;  // 8: 8 rows per warp band, else 16
     s = launch_sweep_cband(g.P, a, count, st);
   } else if (c.variant == kVariantCluster) {
-    if (!fp32) return HZ_ERR_UNSUPPORTED;
+    if (a0.round_mode != 0) return HZ_ERR_UNSUPPORTED;  // 16-bit trials run on the block kernel
     SweepArgs a = a0;
     a.ty_force = c.ty;  // 4: 4P rows per thread, else 2P
-    s = launch_sweep_cluster(g.P, a, count, st);
+    s = fp32 ? launch_sweep_cluster(g.P, a, count, st) : launch_sweep_cluster_f64(g.P, a, count, st);
   } else {
     SweepArgs a = a0;
     a.ty_force = c.ty;
@@ -368,7 +368,7 @@ hz_status autotune(Problem& pr, int precision, int nt, int m_wh, cudaStream_t st
   if (fp32)
     cands = {{kVariantWarp, 1}, {kVariantWarp, 2}, {kVariantWarp, 4}, {kVariantBlock, 1}, {kVariantBlock, 2},
              {kVariantCluster, 0}, {kVariantCluster, 4}, {kVariantClusterBand, 0}, {kVariantClusterBand, 8}};
-  else cands = {{kVariantBlock, 1}, {kVariantBlock, 2}};
+  else cands = {{kVariantBlock, 1}, {kVariantBlock, 2}, {kVariantCluster, 0}, {kVariantCluster, 4}};
   cudaEvent_t e0, e1;
   HZ_CUDA(cudaEventCreate(&e0));
   HZ_CUDA(cudaEventCreate(&e1));
@@ -477,7 +477,8 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
   // choice for this shape (if autotuning ran) or the size heuristic:
   // FP32 -> warp-per-subdomain kernel when compiled for the shape, else one
   // block per subdomain when it fits in 256 threads, else a cluster of
-  // blocks, else the block kernel with up to 1024 threads; FP64 -> block.
+  // blocks, else the block kernel with up to 1024 threads; FP64 -> block,
+  // else (subdomains too large for one block) a cluster of blocks.
   // a warm start (u0) is read by the one-warp and block kernels (and the
   // mapped kernel above); route it to those
   if (u0) {
@@ -535,15 +536,25 @@ hz_status sweep(Problem& pr, int precision, int nt, int m_wh, double wh_tol, con
     if (ls != HZ_OK && want == kVariantClusterBand)
       return fail(HZ_ERR_UNSUPPORTED, "no cluster-of-bands sweep shape fits");
   }
-  if (ls == HZ_ERR_UNSUPPORTED && fp32 &&
-      (want == kVariantCluster || (want == kVariantAuto && !small_block))) {
+  if (ls == HZ_ERR_UNSUPPORTED && !trial &&
+      (want == kVariantCluster || (fp32 && want == kVariantAuto && !small_block))) {
     // HZ_CLUSTER_TY=4 forces 4P rows per thread in the cluster kernel (tests)
     const char* cty = std::getenv("HZ_CLUSTER_TY");
     ls = launch_choice(pr, a, Choice{kVariantCluster, cty ? std::atoi(cty) : 0}, fp32, st);
     if (ls != HZ_OK && ls != HZ_ERR_UNSUPPORTED) return ls;
     if (ls != HZ_OK && want == kVariantCluster) return fail(HZ_ERR_UNSUPPORTED, "no cluster sweep shape fits");
   }
-  if (ls == HZ_ERR_UNSUPPORTED) HZ_TRY(launch_choice(pr, a, Choice{kVariantBlock, 0}, fp32, st));
+  if (ls == HZ_ERR_UNSUPPORTED) {
+    ls = launch_choice(pr, a, Choice{kVariantBlock, 0}, fp32, st);
+    // FP64 (and FP32 forced off the cluster heuristic): subdomains too large
+    // for one block run on a cluster of blocks
+    if (ls == HZ_ERR_UNSUPPORTED && !trial) {
+      const char* cty = std::getenv("HZ_CLUSTER_TY");
+      const hz_status cs = launch_choice(pr, a, Choice{kVariantCluster, cty ? std::atoi(cty) : 0}, fp32, st);
+      if (cs != HZ_ERR_UNSUPPORTED) ls = cs;
+    }
+    HZ_TRY(ls);
+  }
   if (e1) HZ_CUDA(cudaEventRecord(e1, st));
   pr.sweeps_launched++;
   return HZ_OK;

@@ -1,4 +1,4 @@
-// Cluster DD sweep (FP32) for subdomains too large for one thread block.
+// Cluster DD sweep (FP32 or FP64) for subdomains too large for one thread block.
 //
 // A subdomain is split into CN column bands; band q is solved by CTA q of a
 // thread-block cluster (one cluster per subdomain, all subdomains in one
@@ -12,9 +12,15 @@
 // and remote stores visible -- the same single-barrier double-buffer
 // argument as in one block, extended to the cluster.
 //
+// The kernel is compiled for FP32 (hz_sweep_cluster_f32.cu) and FP64
+// (hz_sweep_cluster_f64.cu, the plain-FP64 path for subdomains too large
+// for one block).
+//
 // Arithmetic is that of the block sweep (Algorithm 1; modified leapfrog;
 // eq. (WaveHoltz) with the -1/(i omega) sign and 2/N_t scaling; lambda
 // update -lambda - 2ik u).
+#pragma once
+
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -25,6 +31,18 @@ namespace cg = cooperative_groups;
 namespace hz {
 namespace cluster_sweep {
 namespace {
+
+// 4-wide table entries / edge-column records in the working precision
+template <typename Real>
+struct alignas(4 * sizeof(Real)) Vec4 {
+  Real x, y, z, w;
+};
+template <typename Real>
+__device__ __forceinline__ Real kref(const SweepArgs& a, int k);
+template <>
+__device__ __forceinline__ float kref<float>(const SweepArgs& a, int k) { return a.Kref32[k]; }
+template <>
+__device__ __forceinline__ double kref<double>(const SweepArgs& a, int k) { return a.Kref[k]; }
 
 // Threads per CTA at most: 512 with 2P rows per thread (TY = 2, up to 128
 // registers), 256 with 4P rows (TY = 4, up to 255 registers).
@@ -37,14 +55,14 @@ struct ClusterBlock {
 // and the forcing live only on the subdomain's edges, kept out of the
 // per-thread registers: the first and last node rows in six registers, the
 // edge columns' other rows in a shared table read by the edge threads only.
-template <int P, int TY, int CN, bool SRC>
+template <typename Real, int P, int TY, int CN, bool SRC>
 __global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_kernel(const __grid_constant__ SweepArgs a,
                                                                                    int BW) {
   constexpr int RY = P * TY;
   constexpr int NK = 2 * P + 1;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* sm = reinterpret_cast<float*>(smem_raw);
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
 
   const int q = (int)cluster.block_rank();
   const int l = sweep_subdomain(a, blockIdx.x / CN);
@@ -63,18 +81,18 @@ __global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_k
   const int colsP = BW + 2 * P;
   const int rowsP = a.NS * RY + P + 1;
   const int PS = rowsP * colsP;
-  float* buf0 = sm;
-  float* buf1 = sm + PS;
-  float2* stash = reinterpret_cast<float2*>(sm + 2 * PS);  // previous iterate (tolerance mode)
+  Real* buf0 = sm;
+  Real* buf1 = sm + PS;
+  Real* stash = sm + 2 * PS;  // previous iterate (tolerance mode), (re, im) per node
   // edge-column table (no source): row j of this band's W (slot 0) / E (slot 1) column,
   // at a 16-byte aligned offset after the tiles and the stash
-  float4* ecol = reinterpret_cast<float4*>(sm + ((2 * PS + 2 * nly * BW + 3) & ~3));
+  Vec4<Real>* ecol = reinterpret_cast<Vec4<Real>*>(sm + ((2 * PS + 2 * nly * BW + 3) & ~3));
 
-  for (int k = t; k < 2 * PS; k += blockDim.x) sm[k] = 0.f;
-  float* left0 = q > 0 ? cluster.map_shared_rank(buf0, q - 1) : nullptr;
-  float* left1 = q > 0 ? cluster.map_shared_rank(buf1, q - 1) : nullptr;
-  float* right0 = q < CN - 1 ? cluster.map_shared_rank(buf0, q + 1) : nullptr;
-  float* right1 = q < CN - 1 ? cluster.map_shared_rank(buf1, q + 1) : nullptr;
+  for (int k = t; k < 2 * PS; k += blockDim.x) sm[k] = Real(0);
+  Real* left0 = q > 0 ? cluster.map_shared_rank(buf0, q - 1) : nullptr;
+  Real* left1 = q > 0 ? cluster.map_shared_rank(buf1, q - 1) : nullptr;
+  Real* right0 = q < CN - 1 ? cluster.map_shared_rank(buf0, q + 1) : nullptr;
+  Real* right1 = q < CN - 1 ? cluster.map_shared_rank(buf1, q + 1) : nullptr;
   const bool push_left = active && q > 0 && il < P;
   const bool push_right = active && q < CN - 1 && il >= bw - P;
 
@@ -82,7 +100,7 @@ __global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_k
   const int ax = i % P, ex = i / P;
   const bool own_x = ex < a.sxe;
   const bool left_x = (ax == 0) && (ex >= 1);
-  float kx[NK];
+  Real kx[NK];
 #pragma unroll
   for (int tt = 0; tt < NK; ++tt) {
     const int off = tt - P;
@@ -90,34 +108,34 @@ __global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_k
     const int b = ax + off;
     if (own_x && b >= 0 && b <= P) v += a.Kref[ax * (P + 1) + b];
     if (left_x && off <= 0) v += a.Kref[P * (P + 1) + (off + P)];
-    kx[tt] = (float)(v * a.kxs);
+    kx[tt] = (Real)(v * a.kxs);
   }
-  const float wxy = (float)(a.kys * a.hx2 * ((own_x ? a.w[ax] : 0.0) + (left_x ? a.w[P] : 0.0)));
-  float wy[RY];
-  float eok[TY];
+  const Real wxy = (Real)(a.kys * a.hx2 * ((own_x ? a.w[ax] : 0.0) + (left_x ? a.w[P] : 0.0)));
+  Real wy[RY];
+  Real eok[TY];
 #pragma unroll
   for (int r = 0; r < RY; ++r) {
     const int ay = r % P;
     const int ey = (j0 + r) / P;
     const bool own_y = ey < a.sye;
     const bool below_y = (ay == 0) && (ey >= 1);
-    wy[r] = (float)(a.hy2 * ((own_y ? a.w[ay] : 0.0) + (below_y ? a.w[P] : 0.0)));
+    wy[r] = (Real)(a.hy2 * ((own_y ? a.w[ay] : 0.0) + (below_y ? a.w[P] : 0.0)));
   }
 #pragma unroll
-  for (int qq = 0; qq < TY; ++qq) eok[qq] = (se * TY + qq < a.sye) ? 1.f : 0.f;
-  const float bok = (se > 0) ? 1.f : 0.f;
+  for (int qq = 0; qq < TY; ++qq) eok[qq] = (se * TY + qq < a.sye) ? Real(1) : Real(0);
+  const Real bok = (se > 0) ? Real(1) : Real(0);
 
   // ---- node coefficients and right-hand side
   const int64_t nn = (int64_t)nlx * nly;
-  const float* betaG = static_cast<const float*>(a.beta) + (int64_t)l * nn;
-  const float* alphaG = static_cast<const float*>(a.alpha) + (int64_t)l * nn;
+  const Real* betaG = static_cast<const Real*>(a.beta) + (int64_t)l * nn;
+  const Real* alphaG = static_cast<const Real*>(a.alpha) + (int64_t)l * nn;
   const double* lamL = a.lam_in + (int64_t)l * 4 * a.NE * 2;
   const bool ifW = sxi > 0, ifE = sxi < a.Sx - 1, ifS = syi > 0, ifN = syi < a.Sy - 1;
   constexpr int NR = SRC ? RY : 1;
   const double* kedgeE = a.kedge + (int64_t)l * 4 * a.NE;
-  float bet[RY], alp[NR], bbr[NR], bbi[NR], gam[NR];
+  Real bet[RY], alp[NR], bbr[NR], bbi[NR], gam[NR];
   // no source: first / last node row of the subdomain (all columns), and the edge columns
-  float al0 = 1.f, b0r = 0.f, b0i = 0.f, g0 = 0.f, alN = 1.f, bNr = 0.f, bNi = 0.f, gN = 0.f;
+  Real al0 = 1, b0r = 0, b0i = 0, g0 = 0, alN = 1, bNr = 0, bNi = 0, gN = 0;
   const int slot = (i == 0) ? 0 : (i == nlx - 1) ? 1 : 2;
   const bool edge_col = active && slot < 2;
 #pragma unroll
@@ -147,28 +165,28 @@ __global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_k
       if (j == 0 && ifS) hm += a.wxs[i] * kedgeE[2 * a.NE + i];
       if (j == nly - 1 && ifN) hm += a.wxs[i] * kedgeE[3 * a.NE + i];
     }
-    const float gm = (float)(-be * a.eta * hm);  // gamma = -beta w eta <c^-1 phi, phi>
-    bet[r] = (float)be;
+    const Real gm = (Real)(-be * a.eta * hm);  // gamma = -beta w eta <c^-1 phi, phi>
+    bet[r] = (Real)be;
     if (SRC) {
-      alp[r] = (float)al;
-      bbr[r] = (float)(be * br);
-      bbi[r] = (float)(be * bi);
+      alp[r] = (Real)al;
+      bbr[r] = (Real)(be * br);
+      bbi[r] = (Real)(be * bi);
       gam[r] = gm;
     } else if (live) {
-      if (j == 0) { al0 = (float)al; b0r = (float)(be * br); b0i = (float)(be * bi); g0 = gm; }
-      if (j == nly - 1) { alN = (float)al; bNr = (float)(be * br); bNi = (float)(be * bi); gN = gm; }
+      if (j == 0) { al0 = (Real)al; b0r = (Real)(be * br); b0i = (Real)(be * bi); g0 = gm; }
+      if (j == nly - 1) { alN = (Real)al; bNr = (Real)(be * br); bNi = (Real)(be * bi); gN = gm; }
       if (j > 0 && j < nly - 1 && slot < 2)
-        ecol[j * 2 + slot] = make_float4((float)(al - 1.0), (float)(be * br), (float)(be * bi), gm);
+        ecol[j * 2 + slot] = Vec4<Real>{(Real)(al - 1.0), (Real)(be * br), (Real)(be * bi), gm};
     }
   }
 
-  const float4* tab = static_cast<const float4*>(a.tab);
-  const float sigma = (float)a.sigma, omega = (float)a.omega;
-  const float cpi = (float)a.cpi, spi = (float)a.spi, scale = (float)a.two_over_nt;
+  const Vec4<Real>* tab = static_cast<const Vec4<Real>*>(a.tab);
+  const Real sigma = (Real)a.sigma, omega = (Real)a.omega;
+  const Real cpi = (Real)a.cpi, spi = (Real)a.spi, scale = (Real)a.two_over_nt;
   // u lives in (vre, vim) between WaveHoltz iterations
-  float p[RY], pd[RY], vre[RY], vim[RY];
+  Real p[RY], pd[RY], vre[RY], vim[RY];
 #pragma unroll
-  for (int r = 0; r < RY; ++r) { vre[r] = 0.f; vim[r] = 0.f; }
+  for (int r = 0; r < RY; ++r) { vre[r] = 0; vim[r] = 0; }
   cluster.sync();  // every tile zeroed before any neighbour pushes into it
 
   __shared__ double red[2 * 32];
@@ -184,10 +202,13 @@ __global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_k
     if (check && active) {
 #pragma unroll
       for (int r = 0; r < RY; ++r)
-        if (j0 + r < nly) stash[(j0 + r) * BW + il] = make_float2(vre[r], vim[r]);
+        if (j0 + r < nly) {
+          stash[2 * ((j0 + r) * BW + il)] = vre[r];
+          stash[2 * ((j0 + r) * BW + il) + 1] = vim[r];
+        }
     }
     {
-      const float4 t0 = tab[0];
+      const Vec4<Real> t0 = tab[0];
 #pragma unroll
       for (int r = 0; r < RY; ++r) {
         p[r] = vre[r];
@@ -197,39 +218,39 @@ __global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_k
       }
     }
     for (int nu = 1; nu < a.Nt; ++nu) {
-      const float4 tb = tab[nu];
-      float* bufc = cur ? buf1 : buf0;
+      const Vec4<Real> tb = tab[nu];
+      Real* bufc = cur ? buf1 : buf0;
 #pragma unroll
       for (int r = 0; r < RY; ++r) p[r] += sigma * pd[r];
       if (active) {
 #pragma unroll
         for (int r = 0; r < RY; ++r) bufc[(j0 + r + P) * colsP + il + P] = p[r];
         if (push_left) {
-          float* dst = cur ? left1 : left0;
+          Real* dst = cur ? left1 : left0;
 #pragma unroll
           for (int r = 0; r < RY; ++r) dst[(j0 + r + P) * colsP + BW + P + il] = p[r];
         }
         if (push_right) {
-          float* dst = cur ? right1 : right0;
+          Real* dst = cur ? right1 : right0;
 #pragma unroll
           for (int r = 0; r < RY; ++r) dst[(j0 + r + P) * colsP + il - BW + P] = p[r];
         }
       }
       cluster.sync();
       // y: column values rows j0-P .. j0+RY
-      float col[RY + P + 1];
+      Real col[RY + P + 1];
 #pragma unroll
       for (int k = 0; k < P; ++k) col[k] = bufc[(j0 + k) * colsP + ile + P];
 #pragma unroll
       for (int r = 0; r < RY; ++r) col[P + r] = p[r];
       col[P + RY] = bufc[(j0 + RY + P) * colsP + ile + P];
-      float sy[RY];
+      Real sy[RY];
 #pragma unroll
-      for (int r = 0; r < RY; ++r) sy[r] = 0.f;
+      for (int r = 0; r < RY; ++r) sy[r] = 0;
       {
-        float acc = 0.f;
+        Real acc = 0;
 #pragma unroll
-        for (int b = 0; b <= P; ++b) acc += a.Kref32[P * (P + 1) + b] * col[b];
+        for (int b = 0; b <= P; ++b) acc += kref<Real>(a, P * (P + 1) + b) * col[b];
         sy[0] += bok * acc;
       }
 #pragma unroll
@@ -237,33 +258,33 @@ __global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_k
 #pragma unroll
         for (int aa = 0; aa <= P; ++aa) {
           if (aa == P && qq == TY - 1) continue;  // belongs to the next strip
-          float acc = 0.f;
+          Real acc = 0;
 #pragma unroll
-          for (int b = 0; b <= P; ++b) acc += a.Kref32[aa * (P + 1) + b] * col[P + qq * P + b];
+          for (int b = 0; b <= P; ++b) acc += kref<Real>(a, aa * (P + 1) + b) * col[P + qq * P + b];
           sy[qq * P + aa] += eok[qq] * acc;
         }
       }
 #pragma unroll
       for (int r = 0; r < RY; ++r) {
-        const float* row = bufc + (j0 + r + P) * colsP + ile;
-        float sx = kx[P] * p[r];
+        const Real* row = bufc + (j0 + r + P) * colsP + ile;
+        Real sx = kx[P] * p[r];
 #pragma unroll
         for (int tt = 0; tt < NK; ++tt) {
           if (tt == P) continue;
           sx += kx[tt] * row[tt];
         }
-        const float Ap = wy[r] * sx + wxy * sy[r];
+        const Real Ap = wy[r] * sx + wxy * sy[r];
         if (SRC) {
           pd[r] = alp[r] * pd[r] - bet[r] * Ap + bbr[r] * tb.x + bbi[r] * tb.y + gam[r] * p[r];
         } else {
           const int j = j0 + r;
-          float f = pd[r] - bet[r] * Ap;
+          Real f = pd[r] - bet[r] * Ap;
           if (r % P == 0) {  // only element-boundary rows can be the first or last row
-            if (j == 0) f += (al0 - 1.f) * pd[r] + b0r * tb.x + b0i * tb.y + g0 * p[r];
-            if (j == nly - 1) f += (alN - 1.f) * pd[r] + bNr * tb.x + bNi * tb.y + gN * p[r];
+            if (j == 0) f += (al0 - Real(1)) * pd[r] + b0r * tb.x + b0i * tb.y + g0 * p[r];
+            if (j == nly - 1) f += (alN - Real(1)) * pd[r] + bNr * tb.x + bNi * tb.y + gN * p[r];
           }
           if (edge_col && j > 0 && j < nly - 1) {
-            const float4 e = ecol[j * 2 + slot];
+            const Vec4<Real> e = ecol[j * 2 + slot];
             f += e.x * pd[r] + e.y * tb.x + e.z * tb.y + e.w * p[r];
           }
           pd[r] = f;
@@ -285,8 +306,8 @@ __global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_k
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
           if (j0 + r < nly) {
-            const float2 o = stash[(j0 + r) * BW + il];
-            const double dr = (double)vre[r] - o.x, di = (double)vim[r] - o.y;
+            const Real ox = stash[2 * ((j0 + r) * BW + il)], oy = stash[2 * ((j0 + r) * BW + il) + 1];
+            const double dr = (double)vre[r] - ox, di = (double)vim[r] - oy;
             dn += dr * dr + di * di;
             un += (double)vre[r] * vre[r] + (double)vim[r] * vim[r];
           }
@@ -323,7 +344,7 @@ __global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_k
 
   // ---- epilogue: band-local u in shared memory, then outputs
   bool bad = false;
-  float* su = sm;  // [nly][BW] complex
+  Real* su = sm;  // [nly][BW] complex
   __syncthreads();
   if (active) {
 #pragma unroll
@@ -385,17 +406,17 @@ __global__ void __launch_bounds__(ClusterBlock<TY>::kMaxThreads) sweep_cluster_k
   cluster.sync();  // no CTA leaves while a neighbour may still touch its shared memory
 }
 
-template <int P, int TY, int CN>
+template <typename Real, int P, int TY, int CN>
 hz_status launch(SweepArgs a, int L, int BW, cudaStream_t st) {
   constexpr int RY = P * TY;
   const int threads = ((BW * a.NS + 31) / 32) * 32;
   if (threads > ClusterBlock<TY>::kMaxThreads) return HZ_ERR_UNSUPPORTED;
   const int rowsP = a.NS * RY + P + 1;
   const int colsP = BW + 2 * P;
-  const size_t edge_off = (size_t)((2 * rowsP * colsP + 2 * a.nly * BW + 3) & ~3);  // floats, as in the kernel
-  size_t smem = edge_off * sizeof(float) + (size_t)2 * a.nly * sizeof(float4);
+  const size_t edge_off = (size_t)((2 * rowsP * colsP + 2 * a.nly * BW + 3) & ~3);  // Reals, as in the kernel
+  size_t smem = edge_off * sizeof(Real) + (size_t)2 * a.nly * sizeof(Vec4<Real>);
   if (smem > 220 * 1024) return HZ_ERR_UNSUPPORTED;
-  auto kern = a.rhs ? sweep_cluster_kernel<P, TY, CN, true> : sweep_cluster_kernel<P, TY, CN, false>;
+  auto kern = a.rhs ? sweep_cluster_kernel<Real, P, TY, CN, true> : sweep_cluster_kernel<Real, P, TY, CN, false>;
   HZ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(L * CN));
@@ -414,7 +435,7 @@ hz_status launch(SweepArgs a, int L, int BW, cudaStream_t st) {
   return HZ_OK;
 }
 
-template <int P, int TY>
+template <typename Real, int P, int TY>
 hz_status launch_TY(SweepArgs a, int L, cudaStream_t st) {
   // smallest cluster whose bands fit in one block
   a.NS = (a.nly + TY * P - 1) / (TY * P);
@@ -422,35 +443,36 @@ hz_status launch_TY(SweepArgs a, int L, cudaStream_t st) {
     const int BW = (a.nlx + cn - 1) / cn;
     if (BW * (cn - 1) >= a.nlx || BW < P) continue;  // every band non-empty, halos within one band
     if (((BW * a.NS + 31) / 32) * 32 > ClusterBlock<TY>::kMaxThreads) continue;
-    if (cn == 2) return launch<P, TY, 2>(a, L, BW, st);
-    if (cn == 4) return launch<P, TY, 4>(a, L, BW, st);
-    return launch<P, TY, 8>(a, L, BW, st);
+    if (cn == 2) return launch<Real, P, TY, 2>(a, L, BW, st);
+    if (cn == 4) return launch<Real, P, TY, 4>(a, L, BW, st);
+    return launch<Real, P, TY, 8>(a, L, BW, st);
   }
   return HZ_ERR_UNSUPPORTED;
 }
 
 // Rows per thread 2P (a.ty_force != 4) or 4P (a.ty_force == 4, fewer and
 // fuller threads: more work between cluster barriers).
-template <int P>
+template <typename Real, int P>
 hz_status launch_P(SweepArgs a, int L, cudaStream_t st) {
-  if (a.ty_force == 4) return launch_TY<P, 4>(a, L, st);
-  return launch_TY<P, 2>(a, L, st);
+  if (a.ty_force == 4) return launch_TY<Real, P, 4>(a, L, st);
+  return launch_TY<Real, P, 2>(a, L, st);
+}
+
+template <typename Real>
+hz_status launch_any(int P, const SweepArgs& a, int L, cudaStream_t st) {
+  switch (P) {
+    case 1: return launch_P<Real, 1>(a, L, st);
+    case 2: return launch_P<Real, 2>(a, L, st);
+    case 3: return launch_P<Real, 3>(a, L, st);
+    case 4: return launch_P<Real, 4>(a, L, st);
+    case 5: return launch_P<Real, 5>(a, L, st);
+    case 6: return launch_P<Real, 6>(a, L, st);
+    case 7: return launch_P<Real, 7>(a, L, st);
+    default: return HZ_ERR_UNSUPPORTED;
+  }
 }
 
 }  // namespace
 }  // namespace cluster_sweep
-
-hz_status launch_sweep_cluster(int P, const SweepArgs& a, int L, cudaStream_t st) {
-  switch (P) {
-    case 1: return cluster_sweep::launch_P<1>(a, L, st);
-    case 2: return cluster_sweep::launch_P<2>(a, L, st);
-    case 3: return cluster_sweep::launch_P<3>(a, L, st);
-    case 4: return cluster_sweep::launch_P<4>(a, L, st);
-    case 5: return cluster_sweep::launch_P<5>(a, L, st);
-    case 6: return cluster_sweep::launch_P<6>(a, L, st);
-    case 7: return cluster_sweep::launch_P<7>(a, L, st);
-    default: return HZ_ERR_UNSUPPORTED;
-  }
-}
 
 }  // namespace hz

@@ -350,3 +350,25 @@ def test_warm_started_waveholtz_plain_iteration():
     assert res[True]["wh_iters"] < 0.7 * res[False]["wh_iters"], (res[True]["wh_iters"], res[False]["wh_iters"])
     # the outer iterates agree to the WaveHoltz tolerance, so the sweep counts match
     assert abs(res[True]["sweeps"] - res[False]["sweeps"]) <= 2
+
+
+def test_nested_dissection_direct_solve_equals_plain_direct_solve():
+    """The nested-dissection ordered LU (used for the larger test meshes) is a
+    permutation of the node grid and gives the plain sparse direct solve's
+    result; its separators are element-boundary node lines, which the
+    stiffness does not couple across."""
+    from oracle.sem import nested_dissection_order
+
+    m = sem.Mesh(0, 1, 0, 1, 12, 10, 3, 4, 5)
+    X, Y = m.coords()
+    pr = dd.Problem(m, 1.0 + 0.3 * np.sin(4 * X) * np.cos(3 * Y), 17.0, np.exp(-40 * ((X - .4) ** 2 + (Y - .6) ** 2)))
+    perm = nested_dissection_order(m.NX, m.NY, m.P, leaf=16)
+    assert np.array_equal(np.sort(perm), np.arange(m.NX * m.NY))
+    ud = pr.direct_solve()
+    un = pr.direct_solve(ordering="nd")
+    assert np.max(np.abs(un - ud)) <= 1e-11 * np.max(np.abs(ud))
+    # an element-boundary column separates: no stiffness coupling across it
+    K = pr.matrix().tocoo()
+    I0, I1 = K.row % m.NX, K.col % m.NX
+    s = 2 * m.P
+    assert not np.any((I0 < s) & (I1 > s)) and not np.any((I0 > s) & (I1 < s))
