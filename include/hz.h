@@ -81,6 +81,18 @@ typedef enum { HZ_FP64 = 0, HZ_FP32_REFINE = 1, HZ_FP16_TRIAL = 2, HZ_BF16_TRIAL
  *         fixed WaveHoltz count, where the sweep is only real-linear. */
 typedef enum { HZ_OUTER_GMRES = 0, HZ_OUTER_PLAIN = 1, HZ_OUTER_RGMRES = 2 } hz_outer;
 
+/* FP64 refinement around the DD solves (Sec. 7: the DD cycle is a
+ * preconditioner and may run in lower precision).
+ * DEFECT: defect correction u <- u + DD(b - K u).
+ * FGMRES: flexible GMRES on K u = b in FP64, right-preconditioned by the DD
+ *         solve: each Krylov step is one DD solve (to inner_tol) and one K
+ *         apply; the solution minimises the residual over all corrections of
+ *         a cycle of refine_restart steps.  Converges where defect correction
+ *         stagnates because the FP32 DD solve is accurate to only a fraction
+ *         in a few ill-conditioned directions; costs two global vectors per
+ *         step of the cycle. */
+typedef enum { HZ_REFINE_DEFECT = 0, HZ_REFINE_FGMRES = 1 } hz_refine;
+
 typedef enum {
   HZ_WAVE_SPEED = 0, /* n real values, finite and > 0 (c at every node) */
   HZ_OMEGA = 1,      /* 1 real value > 0 */
@@ -142,11 +154,15 @@ typedef struct {
                             with wh_tol > 0 the WaveHoltz iteration count falls as the outer iteration
                             converges).  The sweep then depends on the previous iterate, so the GMRES
                             outer iterations refuse it (HZ_ERR_INVALID_ARG).  Default 0. */
+  int32_t refine;        /* hz_refine: the FP64 refinement (default HZ_REFINE_DEFECT); with FGMRES,
+                            max_refine bounds the DD solves (preconditioner applications) */
+  int32_t refine_restart; /* FGMRES cycle length, 1..200 (default 30) */
 } hz_solve_opts;
 
 typedef struct {
   int32_t sweeps;        /* DD sweeps (kernel launches of the subdomain solve) */
-  int32_t refinements;   /* FP64 defect-correction steps */
+  int32_t refinements;   /* FP64 refinement steps: defect corrections, or the DD solves applied
+                            as preconditioner by the FGMRES refinement */
   int32_t nt;            /* time steps per period used */
   int32_t wh_iters_max;  /* largest WaveHoltz iteration count of any subdomain */
   double rel_residual;   /* final ||b - K u|| / ||b|| (FP64, global) */
@@ -162,7 +178,8 @@ typedef struct {
 
 /* Defaults: FP64, tol 1e-8, 2000 sweeps, GMRES(60), 20 WaveHoltz iterations,
  * no wh_tol, CFL 0.9, inner_tol 1e-2, 20 refinements, autotune, pack and
- * graphs on, one Gram-Schmidt pass, no warm start. */
+ * graphs on, one Gram-Schmidt pass, no warm start, defect-correction
+ * refinement (FGMRES cycle 30 when selected). */
 HZ_API void hz_default_opts(hz_solve_opts* opts);
 
 /* Copies the calling thread's last error message (NUL-terminated, truncated

@@ -21,6 +21,7 @@ HZ_OK, HZ_ERR_INVALID_ARG, HZ_ERR_OOM, HZ_ERR_CUDA, HZ_ERR_NOT_CONVERGED = 0, 1,
 HZ_ERR_DIVERGED, HZ_ERR_TIMEOUT, HZ_ERR_BUSY, HZ_ERR_NOT_FOUND, HZ_ERR_INTERNAL, HZ_ERR_UNSUPPORTED = 5, 6, 7, 8, 9, 10
 HZ_FP64, HZ_FP32_REFINE, HZ_FP16_TRIAL, HZ_BF16_TRIAL = 0, 1, 2, 3
 HZ_OUTER_GMRES, HZ_OUTER_PLAIN, HZ_OUTER_RGMRES = 0, 1, 2
+HZ_REFINE_DEFECT, HZ_REFINE_FGMRES = 0, 1
 HZ_WAVE_SPEED, HZ_OMEGA, HZ_SOURCE, HZ_BOUNDARY, HZ_TRANSMISSION, HZ_NODE_COORDS = 0, 1, 2, 3, 4, 5
 
 STATUS_NAMES = {0: "HZ_OK", 1: "HZ_ERR_INVALID_ARG", 2: "HZ_ERR_OOM", 3: "HZ_ERR_CUDA", 4: "HZ_ERR_NOT_CONVERGED",
@@ -40,7 +41,7 @@ class hz_solve_opts(C.Structure):
                 ("nt_override", C.c_int32), ("cfl", C.c_double), ("inner_tol", C.c_double),
                 ("max_refine", C.c_int32), ("autotune", C.c_int32), ("wh_adaptive", C.c_int32),
                 ("pack", C.c_int32), ("graphs", C.c_int32), ("gs_passes", C.c_int32),
-                ("wh_warm", C.c_int32)]
+                ("wh_warm", C.c_int32), ("refine", C.c_int32), ("refine_restart", C.c_int32)]
 
 
 class hz_solve_report(C.Structure):

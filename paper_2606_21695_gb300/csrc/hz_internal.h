@@ -138,7 +138,7 @@ hz_status launch_sweep_cluster_f64(int P, const SweepArgs& a, int L, cudaStream_
 
 // FP32 sweep of subdomains wider than 32 node columns by a cluster of CTAs,
 // one per 32-column band, one warp per row band, state in registers (degree
-// 1, 2 or 4; fixed WaveHoltz count).  HZ_ERR_UNSUPPORTED when no compiled
+// 1, 2 or 4; fixed WaveHoltz count or per-subdomain tolerance).  HZ_ERR_UNSUPPORTED when no compiled
 // shape fits.
 hz_status launch_sweep_cband(int P, const SweepArgs& a, int L, cudaStream_t st);
 

@@ -50,6 +50,7 @@ struct hz_problem_s {
   // solver workspace
   hz::DevBuf bvec, rvec, uvec, usub, gv, xv, tv, V, part, small, flags, hcol;
   hz::DevBuf uwarm;  // subdomain solutions carried between sweeps (opts.wh_warm)
+  hz::DevBuf Vg, Zg;  // global Krylov and preconditioned vectors of the FGMRES refinement
   hz::HostBuf hsmall, hcol_host;
   std::vector<cudaEvent_t> gm_events;  // one per Arnoldi step of a cycle
   // CUDA graphs of the Arnoldi step's vector work, one per step index of the

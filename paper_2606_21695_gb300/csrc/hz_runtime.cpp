@@ -931,6 +931,131 @@ hz_status dd_solve(Ctx& c, const double* rhs, double* u) {
   return HZ_OK;
 }
 
+// FP64 flexible GMRES on the global system K u = b, right-preconditioned by
+// the DD solve (Sec. 7: the DD cycle is a preconditioner and may run in
+// lower precision).  Krylov step j applies the preconditioner, z_j = DD(v_j)
+// -- one outer iteration on the transmission data with FP32 (or FP64)
+// sweeps, to inner_tol -- and the global operator, w = K z_j, then two
+// passes of classical Gram-Schmidt on the global vectors.  The z_j are kept
+// because the preconditioner changes from step to step (WaveHoltz with a
+// fixed count is only real-linear, and the inner GMRES stops at a
+// tolerance); u += Z y with y minimising ||beta e1 - H y||.  Every cycle
+// restarts from the true FP64 residual.  Plain defect correction takes the
+// last correction alone; when the FP32 preconditioner is accurate to only a
+// fraction in a few ill-conditioned directions, that stagnates, while the
+// minimisation over all corrections of a cycle removes those directions.
+// rep.refinements counts preconditioner applications.
+hz_status fgmres_refine(Ctx& c, double* u, hz_status* result) {
+  Problem& pr = c.pr;
+  const Geom& g = pr.g;
+  const hz_solve_opts& o = c.o;
+  const int64_t n2 = 2 * g.n;
+  const size_t vb = (size_t)n2 * sizeof(double);
+  const int m = std::max(1, std::min(o.refine_restart, 200));
+  HZ_TRY(pr.Vg.ensure(vb * (m + 1)));
+  HZ_TRY(pr.Zg.ensure(vb * m));
+  double* V = pr.Vg.as<double>();
+  double* Z = pr.Zg.as<double>();
+  Ctx cv{pr, o, c.nt, c.st, c.rep, n2};  // vector work on global vectors
+  HZ_TRY(pr.part.ensure((size_t)std::max(vec_blocks(n2) * (m + 1), axpy_blocks(n2)) * 2 * sizeof(double) + 64));
+  std::vector<cplx> H((size_t)(m + 1) * m), cs(m), sn(m), gvec(m + 1);
+  std::vector<double> hb(4 * (size_t)m + 16);
+  int flags[4];
+  double* sm = pr.small.as<double>();
+  while (true) {
+    // r = b - K u into V_0, with ||r||^2 and ||b||^2
+    HZ_TRY(residual(pr, pr.bvec.as<double>(), u, V, sm, c.st));
+    HZ_TRY(fetch(c, 2, hb.data(), flags));
+    const double bnorm = std::sqrt(hb[1]);
+    const double beta = std::sqrt(hb[0]);
+    const double rel = bnorm > 0.0 ? beta / bnorm : 0.0;
+    c.rep.rel_residual = rel;
+    if (rel <= o.tol) {
+      *result = HZ_OK;
+      return HZ_OK;
+    }
+    if (c.rep.refinements >= o.max_refine || c.rep.sweeps + 2 > o.max_sweeps) {
+      *result = fail(HZ_ERR_NOT_CONVERGED, "tolerance not reached within the refinement / sweep budget");
+      return HZ_OK;
+    }
+    HZ_TRY(launch_axpby(0.0, V, 1.0 / beta, V, n2, c.st));
+    std::fill(gvec.begin(), gvec.end(), cplx(0.0));
+    gvec[0] = beta;
+    int k = 0;
+    double est = rel;
+    for (int j = 0; j < m; ++j) {
+      if (c.rep.refinements >= o.max_refine || c.rep.sweeps + 2 > o.max_sweeps) break;
+      double* vj = V + (size_t)j * n2;
+      double* zj = Z + (size_t)j * n2;
+      double* w = V + (size_t)(j + 1) * n2;
+      // z_j = DD(v_j)
+      HZ_CUDA(cudaMemsetAsync(zj, 0, vb, c.st));
+      hz_solve_opts oi = o;
+      if (o.wh_adaptive) oi.wh_tol = std::min(1e-2, std::max(o.wh_tol > 0.0 ? o.wh_tol : 1e-6, 0.1 * est));
+      Ctx ci{pr, oi, c.nt, c.st, c.rep, c.n2};
+      const hz_status ds = dd_solve(ci, vj, zj);
+      if (ds != HZ_OK && ds != HZ_ERR_NOT_CONVERGED) return ds;
+      c.rep.refinements++;
+      // w = K z_j (the residual kernel with b = 0 gives -K z_j)
+      HZ_TRY(residual(pr, nullptr, zj, w, nullptr, c.st));
+      HZ_TRY(launch_axpby(0.0, w, -1.0, w, n2, c.st));
+      // two passes of classical Gram-Schmidt, then ||w||
+      const int nv = j + 1;
+      HZ_TRY(dots_to(cv, V, n2, nv, w, false, sm));
+      HZ_TRY(launch_multi_axpy(V, n2, nv, sm, w, n2, false, c.st));
+      HZ_TRY(dots_to(cv, V, n2, nv, w, false, sm + 2 * nv));
+      HZ_TRY(launch_multi_axpy(V, n2, nv, sm + 2 * nv, w, n2, false, c.st));
+      HZ_TRY(dots_to(cv, w, 0, 1, w, false, sm + 4 * nv));
+      HZ_TRY(fetch(c, 4 * nv + 2, hb.data(), flags));
+      for (int i = 0; i <= j; ++i)
+        H[(size_t)i * m + j] = cplx(hb[2 * i] + hb[2 * nv + 2 * i], hb[2 * i + 1] + hb[2 * nv + 2 * i + 1]);
+      const double hnext = std::sqrt(std::max(0.0, hb[4 * nv]));
+      if (!(hnext < kGrowthLimit * std::max(1.0, bnorm)) || !std::isfinite(std::abs(H[(size_t)j * m + j])))
+        return fail(HZ_ERR_DIVERGED, "refinement Krylov step exploded: time step beyond the stability limit?");
+      if (hnext > 0.0) HZ_TRY(launch_axpby(0.0, w, 1.0 / hnext, w, n2, c.st));
+      for (int i = 0; i < j; ++i) {
+        const cplx a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * b;
+        H[(size_t)(i + 1) * m + j] = -std::conj(sn[i]) * a + cs[i] * b;
+      }
+      const cplx a = H[(size_t)j * m + j];
+      const double rr = std::sqrt(std::norm(a) + hnext * hnext);
+      if (std::abs(a) == 0.0) {
+        cs[j] = 0.0;
+        sn[j] = 1.0;
+      } else {
+        cs[j] = std::abs(a) / rr;
+        sn[j] = (a / std::abs(a)) * hnext / rr;
+      }
+      H[(size_t)j * m + j] = cs[j] * a + sn[j] * hnext;
+      gvec[j + 1] = -std::conj(sn[j]) * gvec[j];
+      gvec[j] = cs[j] * gvec[j];
+      k = j + 1;
+      est = bnorm > 0.0 ? std::abs(gvec[j + 1]) / bnorm : 0.0;
+      if (est <= 0.5 * o.tol || hnext == 0.0) break;
+    }
+    if (k == 0) {
+      *result = fail(HZ_ERR_NOT_CONVERGED, "tolerance not reached within the refinement / sweep budget");
+      return HZ_OK;
+    }
+    // y from the triangular system, then u += Z y (multi_axpy subtracts: pass -y)
+    std::vector<cplx> y(k);
+    for (int i = k - 1; i >= 0; --i) {
+      cplx s = gvec[i];
+      for (int q = i + 1; q < k; ++q) s -= H[(size_t)i * m + q] * y[q];
+      y[i] = s / H[(size_t)i * m + i];
+    }
+    double* ny = pr.hsmall.as<double>();
+    for (int i = 0; i < k; ++i) {
+      ny[2 * i] = -y[i].real();
+      ny[2 * i + 1] = -y[i].imag();
+    }
+    HZ_CUDA(cudaMemcpyAsync(sm, ny, (size_t)2 * k * sizeof(double), cudaMemcpyHostToDevice, c.st));
+    HZ_TRY(launch_multi_axpy(Z, n2, k, sm, u, n2, false, c.st));
+    HZ_CUDA(cudaStreamSynchronize(c.st));  // the pinned staging buffer is reused
+  }
+}
+
 }  // namespace
 
 hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report* rep_out, cudaStream_t st) {
@@ -941,6 +1066,10 @@ hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report*
     return fail(HZ_ERR_INVALID_ARG, "invalid solve options");
   if (o.outer < HZ_OUTER_GMRES || o.outer > HZ_OUTER_RGMRES) return fail(HZ_ERR_INVALID_ARG, "unknown outer");
   if (o.gs_passes != 1 && o.gs_passes != 2) return fail(HZ_ERR_INVALID_ARG, "gs_passes must be 1 or 2");
+  if (o.refine != HZ_REFINE_DEFECT && o.refine != HZ_REFINE_FGMRES)
+    return fail(HZ_ERR_INVALID_ARG, "unknown refinement");
+  if (o.refine == HZ_REFINE_FGMRES && (o.refine_restart < 1 || o.refine_restart > 200))
+    return fail(HZ_ERR_INVALID_ARG, "refine_restart must be in 1..200");
   if (o.wh_warm != 0 && (o.wh_warm != 1 || o.outer != HZ_OUTER_PLAIN))
     return fail(HZ_ERR_INVALID_ARG, "wh_warm = 1 needs the plain outer iteration (GMRES needs a fixed linear sweep)");
   hz_solve_report rep{};
@@ -970,7 +1099,8 @@ hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report*
   int flags[4];
   hz_status result = HZ_OK;
   double bnorm = 0.0;
-  while (true) {
+  if (o.refine == HZ_REFINE_FGMRES) HZ_TRY(fgmres_refine(c, u, &result));
+  while (o.refine != HZ_REFINE_FGMRES) {
     HZ_TRY(residual(pr, pr.bvec.as<double>(), u, pr.rvec.as<double>(), pr.small.as<double>(), st));
     HZ_TRY(fetch(c, 2, hb, flags));
     bnorm = std::sqrt(hb[1]);
@@ -1140,6 +1270,8 @@ void hz_default_opts(hz_solve_opts* o) {
   o->pack = 1;
   o->graphs = 1;
   o->gs_passes = 1;
+  o->refine = HZ_REFINE_DEFECT;
+  o->refine_restart = 30;
 }
 
 hz_status hz_last_error(char* buf, size_t n) {

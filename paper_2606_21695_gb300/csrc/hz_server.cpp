@@ -74,6 +74,8 @@ uint64_t estimate_bytes(const Geom& g, const hz_solve_opts& o, bool mapped = fal
     b += en * (24 + 12 + 24 + 32) + ns * 16 + nl * 8 + n * 16;
   }
   if (o.wh_warm) b += ns * 16;  // warm-start subdomain solutions
+  if (o.refine == HZ_REFINE_FGMRES)  // global Krylov and preconditioned vectors of a cycle
+    b += n * 16 * (uint64_t)(2 * std::max(1, o.refine_restart) + 1);
   b += n * 8 + n * 16 + (uint64_t)(2 * g.NXg + 2 * g.NYg) * 16;  // c, f, g
   b += 3 * n * 16;                                                 // b, r, u
   b += ns * 16 + ns * 24;                                          // u_sub, alpha/beta (64 + 32 bit)

@@ -1,6 +1,7 @@
 // Cluster of warp bands: FP32 DD sweep (Algorithm 1) for subdomains wider
-// than 32 node columns, degree dividing 32 (P = 1, 2, 4), fixed WaveHoltz
-// count.
+// than 32 node columns, degree dividing 32 (P = 1, 2, 4), a fixed WaveHoltz
+// count or a per-subdomain WaveHoltz tolerance (a cluster-wide reduction of
+// the update norm after every iteration).
 //
 // A subdomain of nlx x NY nodes is cut into column bands of 32 nodes, one CTA
 // of a thread-block cluster each (CN = ceil(nlx / 32) CTAs); inside a CTA the
@@ -63,9 +64,12 @@ struct Smem {
   float hl[2][S::NY][P];        // left column halo: columns c0-P .. c0-1
   float hr[2][S::NY];           // right column halo: column c0+32
   float4 ecol[S::NY];           // this CTA's edge column (W or E): alpha-1, beta b
+  double red[S::W][2];          // tolerance mode: per-warp partial norms
+  double part[2];               // and this CTA's, read by the cluster
+  int stop;
 };
 
-template <int P, int SY, int RB, bool SRC>
+template <int P, int SY, int RB, bool SRC, bool TOL>
 __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int CN, int B, int lane,
                                           Smem<P, SY, RB>& sm, Smem<P, SY, RB>* right, Smem<P, SY, RB>* left,
                                           cg::cluster_group& cluster) {
@@ -166,7 +170,17 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
 
   // buffer parity runs on across WaveHoltz iterations (see the block kernel)
   int cur = 0;
+  int m_done = 0;
+  const int nout = last ? NR : NR - 1;  // row 16 of a band is the next band's row 0
+  float ore[TOL ? NR : 1], oim[TOL ? NR : 1];  // previous iterate (tolerance mode)
   for (int m = 0; m < m_wh; ++m) {
+    if (TOL) {
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        ore[r] = vre[r];
+        oim[r] = vim[r];
+      }
+    }
     {
       const float4 t0 = tab[0];
 #pragma unroll
@@ -254,10 +268,56 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
       vre[r] *= scale;  // u^{(m+1)} = (2/N_t) v
       vim[r] *= scale;
     }
+    m_done = m + 1;
+    if (TOL) {
+      // per-subdomain stop: ||u^{m+1} - u^m|| <= wh_tol ||u^{m+1}|| over the
+      // whole subdomain; partial sums per warp, per CTA, then every CTA adds
+      // the cluster's partials in the same order, so all take the same decision
+      double dn = 0.0, un = 0.0;
+      if (live) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          if (r >= nout) break;
+          const double dr = (double)vre[r] - ore[r], di = (double)vim[r] - oim[r];
+          dn += dr * dr + di * di;
+          un += (double)vre[r] * vre[r] + (double)vim[r] * vim[r];
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        dn += __shfl_xor_sync(0xffffffffu, dn, o);
+        un += __shfl_xor_sync(0xffffffffu, un, o);
+      }
+      if (lane == 0) {
+        sm.red[B][0] = dn;
+        sm.red[B][1] = un;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double D = 0.0, U = 0.0;
+        for (int w = 0; w < W; ++w) {
+          D += sm.red[w][0];
+          U += sm.red[w][1];
+        }
+        sm.part[0] = D;
+        sm.part[1] = U;
+      }
+      cluster.sync();
+      if (threadIdx.x == 0) {
+        double D = 0.0, U = 0.0;
+        for (int r = 0; r < CN; ++r) {
+          const double* pr = cluster.map_shared_rank(sm.part, r);
+          D += pr[0];
+          U += pr[1];
+        }
+        sm.stop = (D <= a.wh_tol * a.wh_tol * U) ? 1 : 0;
+      }
+      cluster.sync();  // remote reads of part[] done, stop visible to the CTA
+      if (sm.stop) break;
+    }
   }
 
   // ---- outputs (row 16 of a band is the next band's row 0: written once, by that band)
-  const int nout = last ? NR : NR - 1;
   bool bad = false;
   if (live) {
 #pragma unroll
@@ -273,8 +333,8 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.flags, 1);
   if (q == 0 && first && lane == 0 && a.wh_iter_max) {
-    atomicMax(a.wh_iter_max, m_wh);
-    atomicAdd(a.wh_iter_sum, (unsigned long long)m_wh);
+    atomicMax(a.wh_iter_max, m_done);
+    atomicAdd(a.wh_iter_sum, (unsigned long long)m_done);
   }
   const int NE = a.NE;
   auto put = [&](int e, int t, bool has, double ur, double ui) {
@@ -318,7 +378,7 @@ __device__ __forceinline__ void band_body(const SweepArgs& a, int l, int q, int 
   }
 }
 
-template <int P, int SY, int RB, bool SRC>
+template <int P, int SY, int RB, bool SRC, bool TOL>
 __global__ void __launch_bounds__(Shape<P, SY, RB>::W * 32) sweep_cband_kernel(const __grid_constant__ SweepArgs a) {
   __shared__ Smem<P, SY, RB> sm;
   cg::cluster_group cluster = cg::this_cluster();
@@ -334,7 +394,7 @@ __global__ void __launch_bounds__(Shape<P, SY, RB>::W * 32) sweep_cband_kernel(c
   Smem<P, SY, RB>* right = q < CN - 1 ? cluster.map_shared_rank(&sm, q + 1) : nullptr;
   Smem<P, SY, RB>* left = q > 0 ? cluster.map_shared_rank(&sm, q - 1) : nullptr;
   cluster.sync();  // every CTA's buffers zeroed before any neighbour pushes into them
-  band_body<P, SY, RB, SRC>(a, l, q, CN, w, lane, sm, right, left, cluster);
+  band_body<P, SY, RB, SRC, TOL>(a, l, q, CN, w, lane, sm, right, left, cluster);
   cluster.sync();  // no CTA leaves while a neighbour may still touch its shared memory
 }
 
@@ -343,7 +403,9 @@ hz_status launch(const SweepArgs& a, int L, cudaStream_t st) {
   using S = Shape<P, SY, RB>;
   const int CN = (a.nlx + 31) / 32;
   if (CN < 2 || CN > 8) return HZ_ERR_UNSUPPORTED;
-  auto kern = a.rhs ? sweep_cband_kernel<P, SY, RB, true> : sweep_cband_kernel<P, SY, RB, false>;
+  const bool tol = a.wh_tol > 0.0;
+  auto kern = a.rhs ? (tol ? sweep_cband_kernel<P, SY, RB, true, true> : sweep_cband_kernel<P, SY, RB, true, false>)
+                    : (tol ? sweep_cband_kernel<P, SY, RB, false, true> : sweep_cband_kernel<P, SY, RB, false, false>);
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(L * CN));
   cfg.blockDim = dim3((unsigned)(S::W * 32));
@@ -376,7 +438,7 @@ hz_status launch_rb(const SweepArgs& a, int L, cudaStream_t st) {
 }  // namespace cband
 
 hz_status launch_sweep_cband(int P, const SweepArgs& a, int L, cudaStream_t st) {
-  if (a.wh_tol > 0.0 || a.round_mode != 0) return HZ_ERR_UNSUPPORTED;  // fixed WaveHoltz count, FP32 only
+  if (a.round_mode != 0) return HZ_ERR_UNSUPPORTED;  // FP32 only
   if (a.nlx <= 32) return HZ_ERR_UNSUPPORTED;
   // rows per warp band: 16 (a.ty_force != 8) or 8
   const int sy = (a.nly - 1) / P;
