@@ -115,17 +115,22 @@ class Problem:
     def direct_solve(self, b=None, ordering="default"):
         """K^{-1} b by a sparse LU.  ordering="nd": the matrix is permuted by
         nested dissection of the node grid first (sem.nested_dissection_order)
-        and factorised in that order with diagonal pivots (the same LU, with
-        far less fill on meshes of 10^5 nodes)."""
+        and factorised in that order with diagonal pivots (far less fill on
+        meshes of 10^5 nodes); without pivoting the factors are less accurate
+        (residual 4e-10 on the 148k-node channel mesh), so two steps of FP64
+        iterative refinement with the same factors follow (x += LU^{-1}(b - K x):
+        residual 9e-15 there)."""
         b = self.rhs() if b is None else b
         if ordering != "nd":
             return spla.spsolve(self.matrix(), b.ravel()).reshape(b.shape)
         m = self.mesh
         perm = nested_dissection_order(m.NX, m.NY, m.P)
-        K = self.matrix()
-        lu = spla.splu(K[perm][:, perm].tocsc(), permc_spec="NATURAL", diag_pivot_thresh=0.0,
-                       options=dict(SymmetricMode=True))
-        up = lu.solve(b.ravel()[perm])
+        Kp = self.matrix()[perm][:, perm].tocsc()
+        lu = spla.splu(Kp, permc_spec="NATURAL", diag_pivot_thresh=0.0, options=dict(SymmetricMode=True))
+        bp = b.ravel()[perm]
+        up = lu.solve(bp)
+        for _ in range(2):
+            up = up + lu.solve(bp - Kp @ up)
         u = np.empty_like(up)
         u[perm] = up
         return u.reshape(b.shape)

@@ -366,7 +366,9 @@ def test_nested_dissection_direct_solve_equals_plain_direct_solve():
     assert np.array_equal(np.sort(perm), np.arange(m.NX * m.NY))
     ud = pr.direct_solve()
     un = pr.direct_solve(ordering="nd")
-    assert np.max(np.abs(un - ud)) <= 1e-11 * np.max(np.abs(ud))
+    assert np.max(np.abs(un - ud)) <= 1e-12 * np.max(np.abs(ud))
+    b = pr.rhs()
+    assert np.linalg.norm(pr.residual(un, b)) <= 1e-13 * np.linalg.norm(b)
     # an element-boundary column separates: no stiffness coupling across it
     K = pr.matrix().tocoo()
     I0, I1 = K.row % m.NX, K.col % m.NX
