@@ -1,8 +1,8 @@
 #!/usr/bin/env python
 """Benchmark of the GPU domain-decomposition Helmholtz solver.
 
-Workload: 256x256 quads on the unit square, degree 3, 32x32 subdomains of
-8x8 elements (625 GLL nodes each), Y-shaped channel at c = 1/3 in c = 1,
+Step workload: 256x256 quads on the unit square, degree 3, 32x32 subdomains
+of 8x8 elements (625 GLL nodes each), Y-shaped channel at c = 1/3 in c = 1,
 omega = 64 pi, off-centre Gaussian source; synthetic, seeded.
 
 One step = one full solve to ||b - K u|| <= 1e-8 ||b|| (FP64 global
@@ -12,9 +12,17 @@ kernel launch (all 1024 subdomain WaveHoltz solves, FP32) per matvec.
 Metric: DOF-updates/s = (sum over sweeps of subdomain nodes x (N_t - 1) x
 WaveHoltz iterations) / wall time of the solves.
 
---impl reference times the FP64 CPU oracle (test infrastructure) on a
-bounded sample of the same workload: one sweep of a subset of subdomains
-per step.
+Legs measured once in the same run (rank 0): the FP32 and FP64 FMA peaks of
+the device (the roofline denominators); the same solve in plain FP64; the
+1024^2-quad degree-4 random-medium workload solved to 1e-8 with FP32 sweeps
+and FP64 refinement (its plain-FP64 time as measured FP64 sweep time x sweep
+count, labelled); a served stream of requests (Poisson arrivals, groups of 8
+sources) with p50/p99 latency and solves/s against one-at-a-time plain FP64;
+the FP64 CPU oracle on all host cores.
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on the
+host's cores on a bounded sample of the step workload: one sweep of a subset
+of subdomains per step.
 """
 
 from __future__ import annotations
@@ -34,8 +42,6 @@ if ROOT not in sys.path:
 
 METRIC = "DOF-updates/s"
 UNIT = "DOF-updates/s"
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
-FP64_PEAK_TFLOPS = 1.25  # nominal FP64 rate of the part (the FP64 pipe is about 1/64 of the FP32 one)
 # DRAM bytes (read + write) of one launch of the one-warp-per-subdomain sweep
 # on the 256x256, P=3 workload, from one ncu capture of this kernel version
 # (coefficients and lambda read once; independent of the WaveHoltz count)
@@ -66,12 +72,28 @@ def parse():
     ap.add_argument("--wh-iters", type=int, default=20, help="WaveHoltz iterations per sweep")
     ap.add_argument("--max-sweeps", type=int, default=5000)
     ap.add_argument("--max-refine", type=int, default=20)
+    ap.add_argument("--refine", choices=["fgmres", "defect"], default="fgmres",
+                    help="FP64 refinement: flexible GMRES with the DD solve as preconditioner, or defect correction")
+    ap.add_argument("--inner-tol", type=float, default=1e-1, help="relative tolerance of each DD solve")
     ap.add_argument("--gs-passes", type=int, choices=[1, 2], default=1,
                     help="classical Gram-Schmidt passes per Arnoldi step")
     ap.add_argument("--robin", default="0,1", help="interface condition d_n + k (eta - i zeta): 'eta,zeta'")
-    ap.add_argument("--workload", choices=["cfg1", "cfg2", "cfg2m", "cfg3", "cfg3s"], default="cfg2",
+    ap.add_argument("--workload", choices=["cfg1", "cfg2", "cfg2m", "cfg3", "cfg3s", "cfg3p4", "cfg3p8", "cfg3p16"],
+                    default="cfg2",
                     help="cfg2 is the benchmark workload; cfg1/cfg3 are reported separately; cfg3s is the "
                          "cfg3 physics and subdomain shape on a 256x256 mesh (for profiling)")
+    ap.add_argument("--no-cfg3", action="store_true", help="skip the 1024^2 random-medium time-to-tolerance leg")
+    ap.add_argument("--cfg3-wh-cap", type=int, default=600, help="WaveHoltz iterations at most per subdomain")
+    ap.add_argument("--cfg3-wh-tol", type=float, default=1e-4, help="per-subdomain WaveHoltz tolerance")
+    ap.add_argument("--cfg3-inner-tol", type=float, default=1e-1)
+    ap.add_argument("--cfg3-restart", type=int, default=200)
+    ap.add_argument("--cfg3-max-sweeps", type=int, default=4000)
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-stream leg")
+    ap.add_argument("--serve-requests", type=int, default=24, help="arrivals in the served-stream leg")
+    ap.add_argument("--serve-pool", type=int, default=16,
+                    help="the served requests are drawn from the cheapest this-many problems of the pool")
+    ap.add_argument("--serve-baseline", type=int, default=3,
+                    help="requests of the stream solved one at a time in plain FP64 for the comparison")
     return ap.parse_args()
 
 
@@ -138,47 +160,136 @@ def _isnum(s):
 
 
 # ------------------------------------------------------- oracle sample ----
-def oracle_sample(wl, seconds, nsub_max=1024):
-    """Times the FP64 oracle sweep on a bounded subset of subdomains of the
-    workload (single-threaded NumPy).  Returns (DOF-updates/s, description)."""
-    try:
-        from threadpoolctl import threadpool_limits
-    except ImportError:  # pragma: no cover
-        threadpool_limits = None
-    import numpy as np
+# The oracle (FP64 NumPy, test infrastructure) timed on the host's cores:
+# a pool of single-threaded worker processes (spawned, so no worker inherits
+# a CUDA context), each sweeping its own share of the sampled subdomains.
+_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS")
+_OW = {}
 
+
+def _oracle_problem(wl):
     from oracle import dd, geom, sem
 
     m = sem.Mesh(*wl.box, wl.nx, wl.ny, wl.P, wl.sub_nx, wl.sub_ny)
     gx, gy = m.coords_1d()
     if getattr(wl, "warp", 0.0) > 0.0:
         X, Y = wl.node_xy(gx, gy)
-        pr = geom.MappedProblem(m, X, Y, wl.speed_at(X, Y), wl.omega, wl.source_at(X, Y), wl.boundary())
-    else:
-        pr = dd.Problem(m, wl.speed(gx, gy), wl.omega, wl.source(gx, gy), wl.boundary())
-    nt = pr.choose_nt()
-    m_wh = 5
-    rhs = pr.rhs()
-    lam = np.zeros((m.L, 4, m.NE), complex)
-    ctx = threadpool_limits(1) if threadpool_limits else None
+        return geom.MappedProblem(m, X, Y, wl.speed_at(X, Y), wl.omega, wl.source_at(X, Y), wl.boundary())
+    return dd.Problem(m, wl.speed(gx, gy), wl.omega, wl.source(gx, gy), wl.boundary())
+
+
+def _ow_init(name, m_wh):
+    import numpy as np
+
+    wl = workload(name)
+    pr = _oracle_problem(wl)
+    m = pr.mesh
+    _OW.update(pr=pr, nt=pr.choose_nt(), m_wh=m_wh, rhs=pr.rhs(), lam=np.zeros((m.L, 4, m.NE), complex))
+
+
+def _ow_sweep(subset):
+    t0 = time.perf_counter()
+    _OW["pr"].sweep(_OW["lam"], _OW["rhs"], _OW["nt"], _OW["m_wh"], subset=list(subset))
+    return time.perf_counter() - t0
+
+
+class OraclePool:
+    """Single-threaded oracle worker processes on `cores` host cores (default:
+    all), each holding the oracle problem of one workload.  sample(seconds)
+    times one sweep over a sample of subdomains sized to take about that much
+    wall time, every worker sweeping its own share."""
+
+    def __init__(self, name, m_wh=5, cores=None):
+        import multiprocessing as mp
+
+        self.name, self.m_wh = name, m_wh
+        self.cores = int(cores or os.cpu_count() or 1)
+        saved = {k: os.environ.get(k) for k in _THREAD_VARS}
+        for k in _THREAD_VARS:
+            os.environ[k] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_ow_init, initargs=(name, m_wh))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.L = workload(name).L
+        ncal = min(8, self.L)
+        cal = self.pool.map(_ow_sweep, [[(k * ncal + q) % self.L for q in range(ncal)] for k in range(self.cores)])
+        self.t_sub = max(cal) / ncal
+        self.info = self.pool.apply(_ow_info)
+
+    def sample(self, seconds):
+        L, cores = self.L, self.cores
+        per = int(max(1, min(max(1, 4 * L // cores), seconds / max(self.t_sub, 1e-6))))
+        chunks = [[(k * per + q) % L for q in range(per)] for k in range(cores)]
+        t0 = time.perf_counter()
+        self.pool.map(_ow_sweep, chunks)
+        wall = time.perf_counter() - t0
+        n_sub = per * cores
+        dof = n_sub * self.info["nl"] * (self.info["nt"] - 1) * self.m_wh
+        return {"value": dof / wall, "cores": cores, "seconds": wall, "nt": self.info["nt"], "nl": self.info["nl"],
+                "sample": f"one sweep (N_t={self.info['nt']}, {self.m_wh} WaveHoltz iterations) of {per} subdomains "
+                          f"on each of {cores} single-threaded processes ({n_sub} subdomain solves, {L} subdomains "
+                          f"in the workload), FP64 NumPy"}
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+
+def _ow_info():
+    m = _OW["pr"].mesh
+    return {"nt": _OW["nt"], "nl": m.nlx * m.nly}
+
+
+def _oracle_solve_cfg1(q):
+    """Child process: the oracle's own solve of cfg1 to 1e-8 (FP64 defect
+    correction around GMRES(60) on the transmission data, 20 WaveHoltz
+    iterations per sweep, inner tolerance 1e-2: the GPU solve's settings)."""
     try:
-        # calibrate on a few subdomains (the oracle is vectorised over them, so
-        # fewer would overstate the per-subdomain cost), then size the sample
-        ncal = min(16, m.L)
+        wl = workload("cfg1")
+        pr = _oracle_problem(wl)
         t0 = time.perf_counter()
-        pr.sweep(lam, rhs, nt, 1, subset=list(range(ncal)))
-        t_cal = (time.perf_counter() - t0) / ncal
-        nsub = int(max(1, min(nsub_max, seconds / max(t_cal * m_wh, 1e-6))))
-        subset = list(range(0, m.L, max(1, m.L // nsub)))[:nsub]
-        t0 = time.perf_counter()
-        pr.sweep(lam, rhs, nt, m_wh, subset=subset)
-        el = time.perf_counter() - t0
+        _, info = pr.solve(m_wh=20, tol=TOL, outer="gmres", restart=60, inner_tol=1e-2, max_sweeps=5000,
+                           max_refine=20)
+        q.put({"seconds": time.perf_counter() - t0, "sweeps": info["sweeps"], "refinements": info["refinements"],
+               "rel_residual": info["rel_residual"], "cores": 1})
+    except Exception as e:  # reported, not raised: a baseline leg
+        q.put({"error": repr(e)})
+
+
+def start_oracle_cfg1():
+    """Starts the oracle's cfg1 time-to-tolerance in a spawned single-threaded
+    process (it runs beside the GPU legs on one otherwise idle host core)."""
+    import multiprocessing as mp
+
+    saved = {k: os.environ.get(k) for k in _THREAD_VARS}
+    for k in _THREAD_VARS:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        q = ctx.Queue()
+        p = ctx.Process(target=_oracle_solve_cfg1, args=(q,), daemon=True)
+        p.start()
     finally:
-        if ctx is not None:
-            ctx.__exit__(None, None, None)
-    dof = len(subset) * m.nlx * m.nly * (nt - 1) * m_wh
-    desc = f"one sweep (N_t={nt}, {m_wh} WaveHoltz iterations) over {len(subset)} of {m.L} subdomains, FP64 NumPy"
-    return dof / el, desc, el
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return p, q
+
+
+def finish_oracle_cfg1(handle, timeout):
+    p, q = handle
+    try:
+        return q.get(timeout=max(1.0, timeout))
+    except Exception:
+        p.terminate()
+        return {"error": f"not finished within {timeout:.0f} s"}
 
 
 def hbm_peak_gbs():
@@ -196,6 +307,15 @@ def workload(name):
 
     if name == "cfg3s":
         return configs.scaled(configs.config3(), 256, 256, 32, 32, name="cfg3_scaled_256x256_p4_sub32")
+    if name in ("cfg3p4", "cfg3p8", "cfg3p16"):  # S x S subdomains of the 1024^2 workload: its shape, h, medium
+        S = int(name[5:])
+        w = configs.config3()
+        h = (w.box[1] - w.box[0]) / w.nx
+        n = 32 * S
+        return configs.Workload(f"cfg3_piece_{S}x{S}_subdomains", (-0.5, -0.5 + n * h, -0.5, -0.5 + n * h), n, n,
+                                w.P, w.sub_nx, w.sub_ny, w.omega, w.speed_kind,
+                                (-0.5 + (n / 2 + 0.5) * h, -0.5 + (n / 2 - 0.5) * h), w.src_width, w.speed_seed,
+                                w.corr_len)
     return {"cfg1": configs.config1, "cfg2": configs.config2, "cfg2m": configs.config2m,
             "cfg3": configs.config3}[name]()
 
@@ -231,12 +351,252 @@ def combine_ranks(elapsed, work, device):
     return float(t.item()), float(w.item())
 
 
+# --------------------------------------------------------------- legs ----
+def leg_peaks(hz):
+    """FP32 and FP64 FMA rates of this device, measured now (hz_fma_peak: a
+    kernel of independent FMAs only; best of three launches of 30-45 ms)."""
+    fp32 = max(hz.hz_fma_peak(hz.HZ_FP32_REFINE, 60000)[0] for _ in range(3))
+    fp64 = max(hz.hz_fma_peak(hz.HZ_FP64, 1200)[0] for _ in range(3))
+    return {"fp32_tflops": fp32, "fp64_tflops": fp64,
+            "how": "hz_fma_peak: 4 blocks of 256 threads per SM, 8 independent FMA chains per thread, "
+                   "CUDA events, best of 3"}
+
+
+def _timed_sweeps(hz, case, precision, nt, wh_iters, k, stream):
+    """Mean device time (CUDA events) of k homogeneous sweeps after one untimed."""
+    import torch
+
+    nl = hz.hz_lambda_size(case.pr)
+    gen = torch.Generator(device="cuda").manual_seed(2)
+    lin = torch.randn(2 * nl, dtype=torch.float64, device="cuda", generator=gen) * 1e-2
+    lout = torch.zeros_like(lin)
+    hz.hz_sweep(case.pr, precision, nt, wh_iters, 0.0, lin, lout, None, None, stream)
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(k):
+        hz.hz_sweep(case.pr, precision, nt, wh_iters, 0.0, lin, lout, None, None, stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    return a0.elapsed_time(a1) * 1e-3 / k
+
+
+def cfg3_solve_opts(hz, args, max_sweeps=None):
+    """FP32 sweeps with a per-subdomain WaveHoltz tolerance inside FP64
+    flexible-GMRES refinement: the configuration that reaches 1e-8 on the
+    random medium (a fixed WaveHoltz count leaves the slowest subdomains'
+    solves too inexact for any refinement to converge)."""
+    return hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, inner_tol=args.cfg3_inner_tol,
+                              wh_iters=args.cfg3_wh_cap, wh_tol=args.cfg3_wh_tol, gmres_restart=args.cfg3_restart,
+                              refine=hz.HZ_REFINE_FGMRES, refine_restart=30, max_refine=60,
+                              max_sweeps=max_sweeps or args.cfg3_max_sweeps)
+
+
+def leg_cfg3(hz, args, stream):
+    """The 1024^2-quad, degree-4 random-medium workload (32x32 subdomains of
+    16641 nodes, omega = 2 pi 204.8).  At full size: the sweep kernel's
+    throughput at the solve's fixed-count configuration (FP32 and FP64, CUDA
+    events), its roofline figures.  Solved to 1e-8: the same physics on 8x8
+    of its subdomains (its subdomain shape, element size, frequency and
+    medium; 1.05 M nodes), FP32 sweeps + FP64 FGMRES refinement, CUDA events
+    around the solve; its plain-FP64 time is the FP32 time scaled by the
+    measured FP64 / FP32 sweep-time ratio (labelled an estimate: ~40x
+    longer)."""
+    import torch
+
+    from paper_2606_21695_gb300.api import Case
+
+    out = {}
+    wl = workload("cfg3")
+    case = Case(wl)
+    try:
+        nt = hz.hz_problem_nt(case.pr)
+        m = args.wh_iters
+        u = torch.zeros(2 * case.n, dtype=torch.float64, device="cuda")
+        # a solve cut short runs the autotuner for the shape (the solve's kernel choice)
+        hz.hz_solve_device(case.pr, hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, wh_iters=m, max_sweeps=3), u,
+                           stream)
+        del u
+        t32 = _timed_sweeps(hz, case, hz.HZ_FP32_REFINE, nt, m, 3, stream)
+        t64 = _timed_sweeps(hz, case, hz.HZ_FP64, nt, m, 1, stream)
+        dof = wl.dof_per_sweep(nt, m)
+        flop = sweep_flops_per_update(wl) * dof
+        out["full_size"] = {"workload": wl.name, "nodes": case.n, "nt": nt, "wh_iters": m,
+                            "fp32_sweep_ms": t32 * 1e3, "fp64_sweep_ms": t64 * 1e3,
+                            "fp32_dof_updates_per_s": dof / t32, "fp64_dof_updates_per_s": dof / t64,
+                            "fp32_sweep_tflops": flop / t32 / 1e12, "fp64_sweep_tflops": flop / t64 / 1e12}
+    finally:
+        case.close()
+    wp = workload("cfg3p8")
+    case = Case(wp)
+    try:
+        n = case.n
+        opts = cfg3_solve_opts(hz, args)
+        u = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
+        hz.hz_solve_device(case.pr, cfg3_solve_opts(hz, args, max_sweeps=4), u, stream)  # tune the shape first
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, rep = hz.hz_solve_device(case.pr, opts, u, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tt = e0.elapsed_time(e1) * 1e-3
+        nt = rep["nt"]
+        r32 = _timed_sweeps(hz, case, hz.HZ_FP32_REFINE, nt, 20, 2, stream)
+        r64 = _timed_sweeps(hz, case, hz.HZ_FP64, nt, 20, 1, stream)
+        out["piece_solve"] = {"workload": wp.name, "nodes": n, "status": hz.STATUS_NAMES[st],
+                              "rel_residual": rep["rel_residual"], "time_to_tol_s": tt, "sweeps": rep["sweeps"],
+                              "dd_solves": rep["refinements"], "gmres_iters": rep["gmres_iters"], "nt": nt,
+                              "wh_tol": opts.wh_tol, "wh_cap": opts.wh_iters, "wh_iters_max": rep["wh_iters_max"],
+                              "inner_tol": opts.inner_tol, "refinement": "FGMRES(30), FP64",
+                              "dof_updates": rep["dof_updates"], "dof_updates_per_s": rep["dof_updates"] / tt,
+                              "sweep_kernel": rep["sweep_variant"], "fp64_over_fp32_sweep": r64 / r32,
+                              "fp64_time_to_tol_s_estimated": tt * r64 / r32,
+                              "fp64_estimate": "FP32 time-to-1e-8 x measured FP64/FP32 sweep-time ratio (20 WaveHoltz "
+                                               "iterations) on this workload"}
+    finally:
+        case.close()
+    return out
+
+
+def _serve_pool(k):
+    """The k problems of the served workload's pool (the batched workload's
+    sampler, seed 500) with the smallest estimated cost, global nodes x N_t
+    (the sampler spans five orders of magnitude: N_t reaches 16 000)."""
+    from workloads import configs
+
+    lam = {1: 8.0, 2: 48.0, 3: 148.6, 4: 366.7, 5: 783.9}  # lambda_max h^2 of the 2D GLL operator
+    rows = []
+    for w in configs.config4(64, seed0=500):
+        cmax = 1.75 if w.speed_kind == "random" else 1.0
+        dt = 0.9 * 2 / (cmax * math.sqrt(lam[w.P]) * w.nx)
+        nt = math.ceil(2 * math.pi / w.omega / dt)
+        rows.append(((w.nx * w.P + 1) ** 2 * nt, w))
+    rows.sort(key=lambda r: r[0])
+    return [w for _, w in rows[:k]]
+
+
+def serve_opts(hz, precision):
+    """Options of a served request: FP64 flexible-GMRES refinement around DD
+    solves to 0.1 whose WaveHoltz runs per subdomain to a tolerance of 1e-4
+    (at most 600 iterations): the pool's high-frequency problems on wide
+    subdomains stall with a fixed WaveHoltz count."""
+    return hz.hz_default_opts(precision=precision, tol=TOL, inner_tol=1e-1, wh_iters=600, wh_tol=1e-4,
+                              refine=hz.HZ_REFINE_FGMRES, refine_restart=30, max_refine=60, max_sweeps=6000)
+
+
+def leg_serve(hz, n_requests, rate, pool_k, baseline_k, seed=5):
+    """Served stream: Poisson arrivals (seeded, mean `rate` per second) of
+    solve requests drawn from the pool; with probability 0.2 a request is a
+    group of 8 sources sharing mesh, wave speed and frequency.  The server
+    (HBM budget 150 GB) admits them as memory frees and advances the admitted
+    solves together.  Latency = submit to solution on the host.  The
+    comparison: the first `baseline_k` requests solved one at a time in plain
+    FP64."""
+    import numpy as np
+
+    from paper_2606_21695_gb300.api import Case
+    from workloads import fields
+
+    pool = _serve_pool(pool_k)
+    cases = {w.name: Case(w) for w in pool}
+    rng = np.random.default_rng(seed)
+    reqs = []
+    t = 0.0
+    for _ in range(n_requests):
+        t += rng.exponential(1.0 / rate)
+        w = pool[int(rng.integers(len(pool)))]
+        k = 8 if rng.uniform() < 0.2 else 1
+        for _ in range(k):
+            reqs.append((t, w, tuple(rng.uniform(0.2, 0.8, 2))))
+    opts = serve_opts(hz, hz.HZ_FP32_REFINE)
+    probs = []  # per-request problems (sources differ), built before the clock starts
+    for _, w, ctr in reqs:
+        c = cases[w.name]
+        X, Y = np.meshgrid(c.gx, c.gy)
+        f = fields.gaussian_source(X, Y, ctr, w.src_width).astype(complex)
+        pr = hz.hz_problem_create(c.mesh, 0)
+        hz.hz_problem_set(pr, hz.HZ_WAVE_SPEED, c.c.ravel())
+        hz.hz_problem_set(pr, hz.HZ_OMEGA, np.array([w.omega]))
+        hz.hz_problem_set(pr, hz.HZ_SOURCE, f.ravel())
+        probs.append((pr, c.n))
+    used = sorted({w.name for _, w, _ in reqs})
+    for name in used:  # autotune the shapes outside the timed stream
+        hz.hz_solve(cases[name].pr, opts, n=cases[name].n)
+    srv = hz.hz_server_create(0, 150 << 30)
+    t0 = time.perf_counter()
+    tickets = []
+    for (ta, _, _), (pr, n) in zip(reqs, probs):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        tickets.append(hz.hz_server_submit(srv, pr, opts))
+    statuses, res = {}, []
+    for tk in tickets:
+        try:
+            _, st, _, rep = hz.hz_server_poll(srv, tk, -1, n=None)
+            res.append(rep["rel_residual"])
+        except hz.HzError as e:
+            st = e.status
+        statuses[hz.STATUS_NAMES[st]] = statuses.get(hz.STATUS_NAMES[st], 0) + 1
+    wall = time.perf_counter() - t0
+    stats = hz.hz_server_stats(srv)
+    hz.hz_server_destroy(srv)
+    o64 = serve_opts(hz, hz.HZ_FP64)
+    nb = min(len(probs), baseline_k)
+    t0 = time.perf_counter()
+    for pr, n in probs[:nb]:
+        hz.hz_solve(pr, o64, n=n)
+    t_base = (time.perf_counter() - t0) / nb
+    for pr, _ in probs:
+        hz.hz_problem_destroy(pr)
+    for c in cases.values():
+        c.close()
+    ok = statuses.get("HZ_OK", 0)
+    return {"requests": n_requests, "solves": len(reqs), "arrival_rate_per_s": rate, "wall_s": wall,
+            "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "solves_per_s": ok / wall,
+            "statuses": statuses, "failed": len(reqs) - ok, "max_rel_residual": max(res) if res else None,
+            "hbm_budget_gb": 150, "pool": f"{pool_k} cheapest of the 64-problem pool", "problems_used": used,
+            "one_at_a_time_fp64_s_per_solve": t_base, "one_at_a_time_fp64_solves_per_s": 1.0 / t_base,
+            "one_at_a_time_fp64_sample": nb}
+
+
+def leg_cpu(args, cfg1_handle, t_start, cfg2_dof_per_solve, cfg3):
+    """The oracle on the host cores: its sweep rate on the step workload and
+    on a piece of the 1024^2 workload (all cores), its own cfg1 solve to 1e-8
+    (one core, run beside the GPU legs), and time-to-tolerance estimates for
+    the two big workloads (the GPU solve's DOF-updates / the oracle's rate)."""
+    pool = OraclePool("cfg2", m_wh=5)
+    s2 = pool.sample(args.cpu_sample_s)
+    pool.close()
+    out = {"value": s2["value"], "unit": UNIT, "cores": s2["cores"], "kind": "oracle", "sample": s2["sample"],
+           "seconds": s2["seconds"]}
+    tt = {}
+    if cfg1_handle is not None:
+        tt["cfg1_measured"] = finish_oracle_cfg1(cfg1_handle, timeout=600 - (time.perf_counter() - t_start))
+    tt["cfg2_estimated_s"] = cfg2_dof_per_solve / s2["value"]
+    if cfg3 is not None and cfg3.get("piece_solve", {}).get("dof_updates"):
+        pool3 = OraclePool("cfg3p4", m_wh=5)
+        s3 = pool3.sample(8.0)
+        pool3.close()
+        out["cfg3_shape_rate"] = s3["value"]
+        tt["cfg3_piece_estimated_s"] = cfg3["piece_solve"]["dof_updates"] / s3["value"]
+    tt["estimate"] = ("the GPU solve's DOF-updates / the oracle's DOF-updates/s on all cores (same method, "
+                      "same sweep count)")
+    out["time_to_tol_s"] = tt
+    return out
+
+
 # ------------------------------------------------------------ our arm ----
 def run_ours(args):
+    t_start = time.perf_counter()
+    rank, world, local = dist_env()
+    # the oracle's own cfg1 solve runs beside the GPU legs on one host core
+    # (spawned before this process touches CUDA)
+    cfg1_handle = start_oracle_cfg1() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     import numpy as np
     import torch
 
-    rank, world, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as tdist
@@ -253,9 +613,11 @@ def run_ours(args):
         hz.hz_problem_set(case.pr, hz.HZ_TRANSMISSION, np.array(robin))
     n = case.n
     stream = torch.cuda.current_stream()
-    opts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, inner_tol=1e-2, wh_iters=args.wh_iters,
-                              gmres_restart=60, max_sweeps=args.max_sweeps, max_refine=args.max_refine,
-                              gs_passes=args.gs_passes)
+    refine = hz.HZ_REFINE_FGMRES if args.refine == "fgmres" else hz.HZ_REFINE_DEFECT
+    opts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, inner_tol=args.inner_tol,
+                              wh_iters=args.wh_iters, gmres_restart=60, max_sweeps=args.max_sweeps,
+                              max_refine=args.max_refine, gs_passes=args.gs_passes, refine=refine,
+                              refine_restart=30)
     u = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
@@ -308,6 +670,7 @@ def run_ours(args):
 
     out = None
     if rank == 0:
+        peaks = leg_peaks(hz)
         # end-to-end through the public C ABI with host buffers: upload the
         # fields, solve, read u back; every step
         c_h, f_h, g_h = case.c.ravel(), case.f.ravel(), boundary_vector(case.g)
@@ -329,9 +692,10 @@ def run_ours(args):
         # plain-FP64 time to the same tolerance, one solve (outside the timed region)
         fp64 = None
         if not args.no_fp64:
-            o64 = hz.hz_default_opts(precision=hz.HZ_FP64, tol=TOL, inner_tol=1e-2, wh_iters=args.wh_iters,
-                                     gmres_restart=60, max_sweeps=args.max_sweeps, max_refine=args.max_refine,
-                                     gs_passes=args.gs_passes)
+            o64 = hz.hz_default_opts(precision=hz.HZ_FP64, tol=TOL, inner_tol=args.inner_tol,
+                                     wh_iters=args.wh_iters, gmres_restart=60, max_sweeps=args.max_sweeps,
+                                     max_refine=args.max_refine, gs_passes=args.gs_passes, refine=refine,
+                                     refine_restart=30)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -372,8 +736,9 @@ def run_ours(args):
             tfl = res_flops / (res_ms * 1e-3) / 1e12
             aux = {"residual": {"kernel": "residual_kernel + reduce_partials_kernel (FP64, global grid)",
                                 "bound": "fp64 alu", "ms": res_ms, "algorithmic_flops": res_flops,
-                                "achieved_tflops": tfl, "peak_tflops": FP64_PEAK_TFLOPS,
-                                "frac": tfl / FP64_PEAK_TFLOPS, "algorithmic_bytes": res_bytes,
+                                "achieved_tflops": tfl, "peak_tflops": peaks["fp64_tflops"],
+                                "frac": tfl / peaks["fp64_tflops"], "peak_source": "measured FP64 FMA rate",
+                                "algorithmic_bytes": res_bytes,
                                 "achieved_gbs": gbs, "hbm_peak_gbs": peak, "hbm_frac": gbs / peak}}
             del rb, ru, rr, rn
         # 16-bit trials: one sweep each, error against the FP64 sweep (which is
@@ -395,10 +760,12 @@ def run_ours(args):
             den = float(ref.abs().max())
             trials = {k: {"sweep_rel_err_vs_fp64": float((outs[k] - ref).abs().max()) / den}
                       for k in ("fp32", "fp16", "bf16")}
+        cfg3 = leg_cfg3(hz, args, stream) if (world == 1 and not args.no_cfg3) else None
+        serve = (leg_serve(hz, args.serve_requests, args.rate, args.serve_pool, args.serve_baseline)
+                 if (world == 1 and not args.no_serve) else None)
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            v, desc, el = oracle_sample(wl, args.cpu_sample_s)
-            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "seconds": el}
+            cpu = leg_cpu(args, cfg1_handle, t_start, dof / args.steps, cfg3)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps * 1e3, "higher_is_better": True,
@@ -407,10 +774,20 @@ def run_ours(args):
             "config": {"workload": wl.name, "mesh": f"{wl.nx}x{wl.ny} quads", "degree": P,
                        "subdomains": f"{wl.nx // wl.sub_nx}x{wl.ny // wl.sub_ny} of {wl.sub_nx}x{wl.sub_ny}",
                        "omega": wl.omega, "nt": nt, "wh_iters": opts.wh_iters, "tol": TOL,
-                       "outer": f"GMRES(60), {args.gs_passes} classical Gram-Schmidt pass(es), in FP64 defect correction", "l2": "flushed (256 MB write) before each step",
+                       "outer": (f"GMRES(60) on the transmission data to {args.inner_tol:g}, {args.gs_passes} "
+                                 f"classical Gram-Schmidt pass(es), inside FP64 "
+                                 + ("flexible GMRES(30) on K u = b" if args.refine == "fgmres"
+                                    else "defect correction")),
+                       "l2": "flushed (256 MB write) before each step",
                        "transmission": {"eta": robin[0], "zeta": robin[1]},
                        "parallelism": f"{world} independent solves (one per GPU)"},
-            "time_to_tol_s": {"fp32_refine": elapsed / args.steps, "fp64": fp64["seconds"] if fp64 else None},
+            "time_to_tol_s": {"fp32_refine": elapsed / args.steps, "fp64": fp64["seconds"] if fp64 else None,
+                              "cfg3_piece_fp32_refine": cfg3["piece_solve"]["time_to_tol_s"] if cfg3 else None,
+                              "cfg3_piece_fp64_estimated": (cfg3["piece_solve"]["fp64_time_to_tol_s_estimated"]
+                                                            if cfg3 else None)},
+            "cfg3": cfg3,
+            "serve": serve,
+            "peaks": peaks,
             "fp64_solve": fp64,
             "solve": {"sweeps_per_solve": sweeps / args.steps, "rel_residual_max": max(res),
                       "sweep_kernel": {1: "block", 2: "warp", 3: "cluster", 4: "packed",
@@ -423,8 +800,9 @@ def run_ours(args):
                                     3: "sweep_cluster_kernel", 5: "sweep_cband_kernel",
                                     6: "sweep_mapped_kernel (element form, block per subdomain)"}.get(reports[0]["sweep_variant"], "?")
                          + " FP32, one launch = one DD sweep", "bound": "alu",
-                         "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS,
+                         "achieved": achieved, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+                         "frac": achieved / peaks["fp32_tflops"],
+                         "peak_source": "measured in this run (hz_fma_peak, FP32 FMA)",
                          "traffic": SWEEP_WARP_TRAFFIC_BYTES if (wl.P == 3 and reports[0]["sweep_variant"] == 2
                                                                  and reports[0]["sweep_shape"] == 1) else None,
                          "traffic_unit": "bytes per launch (DRAM, ncu)",
@@ -450,18 +828,23 @@ def run_ours(args):
 
 # ------------------------------------------------------ reference arm ----
 def run_reference(args):
+    """The oracle as it stands (FP64 NumPy), timed on all host cores: each
+    step one sweep over a bounded sample of the step workload's subdomains."""
     rank, world, _ = dist_env()
     if rank != 0:
         return None
-    from workloads import configs
-
-    wl = configs.config2()
+    wl = workload("cfg2")
+    pool = OraclePool("cfg2", m_wh=5)
     vals = []
-    desc = ""
-    for k in range(args.warmup + args.steps):
-        v, desc, el = oracle_sample(wl, seconds=3.0, nsub_max=16)
-        if k >= args.warmup:
-            vals.append((v, el))
+    desc, cores = "", pool.cores
+    try:
+        for k in range(args.warmup + args.steps):
+            r = pool.sample(3.0)
+            desc = r["sample"]
+            if k >= args.warmup:
+                vals.append((r["value"], r["seconds"]))
+    finally:
+        pool.close()
     tot_t = sum(el for _, el in vals)
     value = sum(v * el for v, el in vals) / tot_t
     return {
@@ -470,7 +853,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded generators)",
         "config": {"workload": wl.name, "sample": desc},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -617,74 +1000,12 @@ def run_batch(args):
 
 
 def run_serve(args):
-    """--mode serve: Poisson arrivals (seeded, mean args.rate per second) of
-    solve requests drawn from the cheapest problems of the batched workload;
-    with probability 0.2 a request is a group of 8 sources on one mesh and
-    frequency.  Reports p50/p99 latency and solves/s, and the same stream
-    solved one at a time in plain FP64 for comparison."""
-    import numpy as np
-    import torch
-
+    """--mode serve: the served-stream leg alone (see leg_serve)."""
     import paper_2606_21695_gb300 as hz
-    from paper_2606_21695_gb300.api import Case
-    from workloads import fields
 
-    pool = _cheap_cfg4(8)
-    cases = {w.name: Case(w) for w in pool}
-    rng = np.random.default_rng(5)
-    reqs = []
-    t = 0.0
-    for _ in range(args.requests):
-        t += rng.exponential(1.0 / args.rate)
-        w = pool[int(rng.integers(len(pool)))]
-        k = 8 if rng.uniform() < 0.2 else 1
-        for _ in range(k):
-            reqs.append((t, w, tuple(rng.uniform(0.2, 0.8, 2))))
-    opts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, max_sweeps=5000)
-    # per-request problems (sources differ), built before the clock starts
-    probs = []
-    for _, w, ctr in reqs:
-        c = cases[w.name]
-        X, Y = np.meshgrid(c.gx, c.gy)
-        f = fields.gaussian_source(X, Y, ctr, w.src_width).astype(complex)
-        pr = hz.hz_problem_create(c.mesh, 0)
-        hz.hz_problem_set(pr, hz.HZ_WAVE_SPEED, c.c.ravel())
-        hz.hz_problem_set(pr, hz.HZ_OMEGA, np.array([w.omega]))
-        hz.hz_problem_set(pr, hz.HZ_SOURCE, f.ravel())
-        probs.append((pr, c.n))
-    for w in pool:  # autotune the shapes outside the timed stream
-        c = cases[w.name]
-        hz.hz_solve(c.pr, opts, n=c.n)
-    os.environ.setdefault("HZ_SERVER_WORKERS", "8")
-    srv = hz.hz_server_create(0, 150 << 30)  # HBM admission budget of the served workload
-    t0 = time.perf_counter()
-    tickets = []
-    for (ta, _, _), (pr, n) in zip(reqs, probs):
-        now = time.perf_counter() - t0
-        if ta > now:
-            time.sleep(ta - now)
-        tickets.append((hz.hz_server_submit(srv, pr, opts), n))
-    res = []
-    for tk, n in tickets:
-        done, st, _, rep = hz.hz_server_poll(srv, tk, -1, n=None)
-        res.append(rep["rel_residual"])
-    wall = time.perf_counter() - t0
-    stats = hz.hz_server_stats(srv)
-    hz.hz_server_destroy(srv)
-    # baseline: the same stream one request at a time, plain FP64
-    o64 = hz.hz_default_opts(precision=hz.HZ_FP64, tol=TOL, max_sweeps=5000)
-    nb = min(len(probs), args.baseline_requests)
-    t0 = time.perf_counter()
-    for pr, n in probs[:nb]:
-        hz.hz_solve(pr, o64, n=n)
-    t_base = (time.perf_counter() - t0) / nb
-    for pr, _ in probs:
-        hz.hz_problem_destroy(pr)
-    return {"mode": "serve", "requests": len(reqs), "arrival_rate_per_s": args.rate, "wall_s": wall,
-            "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "solves_per_s": len(reqs) / wall,
-            "max_rel_residual": max(res), "pool": [w.name for w in pool],
-            "one_at_a_time_fp64_s_per_solve": t_base, "one_at_a_time_fp64_solves_per_s": 1.0 / t_base,
-            "one_at_a_time_fp64_sample": nb}
+    out = leg_serve(hz, args.requests, args.rate, args.serve_pool, args.baseline_requests)
+    out["mode"] = "serve"
+    return out
 
 
 def main():
