@@ -44,3 +44,41 @@ def test_combine_ranks_max_time_total_work(world):
         assert t == 1.5 + (world - 1)
         assert w == 1e9 * world * (world + 1) / 2
         assert (r_env, w_env) == (rank, world)
+
+
+def test_bench_workload_pieces_keep_the_big_workload_physics():
+    """The 1024^2 workload's pieces (bench legs, profiles) have its element
+    size, degree, subdomain shape, frequency and medium."""
+    import bench
+
+    w3 = bench.workload("cfg3")
+    h3 = (w3.box[1] - w3.box[0]) / w3.nx
+    for name, S in (("cfg3p4", 4), ("cfg3p8", 8), ("cfg3p16", 16)):
+        w = bench.workload(name)
+        assert w.nx == w.ny == 32 * S and w.L == S * S
+        assert abs((w.box[1] - w.box[0]) / w.nx - h3) < 1e-15
+        assert (w.P, w.sub_nx, w.sub_ny, w.omega, w.speed_kind, w.speed_seed, w.corr_len) == \
+               (w3.P, w3.sub_nx, w3.sub_ny, w3.omega, w3.speed_kind, w3.speed_seed, w3.corr_len)
+
+
+def test_served_pool_is_the_cheapest_draws_of_the_sampler():
+    import bench
+    from workloads import configs
+
+    pool = bench._serve_pool(16)
+    names = {w.name for w in configs.config4(64, seed0=500)}
+    assert len(pool) == 16 and {w.name for w in pool} <= names
+    assert [w.name for w in bench._serve_pool(16)] == [w.name for w in pool]  # deterministic
+
+
+def test_oracle_pool_on_two_cores():
+    """The CPU baseline's worker pool: spawned single-threaded processes, a
+    timed sample with a positive rate."""
+    import bench
+
+    pool = bench.OraclePool("cfg1", m_wh=1, cores=2)
+    try:
+        r = pool.sample(0.2)
+    finally:
+        pool.close()
+    assert r["cores"] == 2 and r["value"] > 0 and r["nl"] == 17 * 17
