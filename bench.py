@@ -531,13 +531,17 @@ def leg_serve(hz, n_requests, rate, pool_k, baseline_k, seed=5):
         if ta > now:
             time.sleep(ta - now)
         tickets.append(hz.hz_server_submit(srv, pr, opts))
-    statuses, res = {}, []
-    for tk in tickets:
+    statuses, res, errors = {}, [], []
+    for k, tk in enumerate(tickets):
         try:
             _, st, _, rep = hz.hz_server_poll(srv, tk, -1, n=None)
             res.append(rep["rel_residual"])
+            if st != hz.HZ_OK:
+                errors.append({"request": k, "problem": reqs[k][1].name, "status": hz.STATUS_NAMES[st],
+                               "rel_residual": rep["rel_residual"], "sweeps": rep["sweeps"]})
         except hz.HzError as e:
             st = e.status
+            errors.append({"request": k, "problem": reqs[k][1].name, "error": str(e)})
         statuses[hz.STATUS_NAMES[st]] = statuses.get(hz.STATUS_NAMES[st], 0) + 1
     wall = time.perf_counter() - t0
     stats = hz.hz_server_stats(srv)
@@ -555,7 +559,8 @@ def leg_serve(hz, n_requests, rate, pool_k, baseline_k, seed=5):
     ok = statuses.get("HZ_OK", 0)
     return {"requests": n_requests, "solves": len(reqs), "arrival_rate_per_s": rate, "wall_s": wall,
             "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "solves_per_s": ok / wall,
-            "statuses": statuses, "failed": len(reqs) - ok, "max_rel_residual": max(res) if res else None,
+            "statuses": statuses, "failed": len(reqs) - ok, "errors": errors,
+            "max_rel_residual": max(res) if res else None,
             "hbm_budget_gb": 150, "pool": f"{pool_k} cheapest of the 64-problem pool", "problems_used": used,
             "one_at_a_time_fp64_s_per_solve": t_base, "one_at_a_time_fp64_solves_per_s": 1.0 / t_base,
             "one_at_a_time_fp64_sample": nb}
