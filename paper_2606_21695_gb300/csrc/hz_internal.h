@@ -31,6 +31,12 @@ void note_launch();  // counts kernel launches (hz_kernel_launches)
     if (s_ != HZ_OK) return s_;          \
   } while (0)
 
+// Host-to-device copies from pageable memory and memsets issued on the legacy
+// default stream may return before the data are in device memory, and the
+// problems' non-blocking streams are not ordered after that stream: every
+// upload of problem data waits for the legacy stream before returning.
+#define HZ_UPLOADS_DONE() HZ_CUDA(cudaStreamSynchronize(nullptr))
+
 // ------------------------------------------------------- device memory ----
 // Owning device buffer (cudaMalloc on the problem's device).
 struct DevBuf {

@@ -228,6 +228,7 @@ hz_status set_node_coords(Problem& pr, const double* xy) {
   HZ_TRY(up(pr.mHw, Hw.data(), Hw.size() * sizeof(double)));
   HZ_TRY(up(pr.mbw, bw.data(), bw.size() * sizeof(double)));
   HZ_TRY(pr.mflux.ensure((size_t)nel * n2 * 4 * sizeof(double)));
+  HZ_UPLOADS_DONE();
   pr.mapped_D = D;
   pr.mapped_mu = mu;
   pr.mapped = true;

@@ -1233,6 +1233,7 @@ hz_status set_field_host(Problem& pr, hz_field field, const double* data, int64_
       HZ_TRY(set_node_coords(pr, data));
       break;
   }
+  HZ_UPLOADS_DONE();
   pr.version++;
   return HZ_OK;
 }
@@ -1348,6 +1349,7 @@ hz_status hz_problem_create(hz_mesh mesh, int32_t device, hz_problem* out) {
       const size_t nbd = (size_t)(2 * g.NXg + 2 * g.NYg) * 2 * sizeof(double);
       HZ_TRY(pr->gb.ensure(nbd));
       HZ_CUDA(cudaMemset(pr->gb.ptr, 0, nbd));
+      HZ_UPLOADS_DONE();
       HZ_CUDA(cudaStreamCreateWithFlags(&pr->stream, cudaStreamNonBlocking));
       return HZ_OK;
     }();

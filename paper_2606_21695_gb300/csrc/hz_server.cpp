@@ -116,21 +116,23 @@ hz_status snapshot_problem(const hz_problem_s& src, Request* req) {
   return HZ_OK;
 }
 
-// Copies an admitted request's fields to the device and gives it a stream;
-// the host snapshot is dropped.
+// Gives an admitted request a stream and copies its fields to the device on
+// it (the solve that follows on the same stream is ordered after the copies;
+// the stream is synchronised before the host snapshot is dropped).
 hz_status materialize(Request* req) {
   hz_problem_s& pr = *req->pr;
   HZ_CUDA(cudaSetDevice(pr.device));
+  HZ_CUDA(cudaStreamCreateWithFlags(&pr.stream, cudaStreamNonBlocking));
   for (int k = 0; k < kNumFieldBufs; ++k) {
     std::vector<unsigned char>& h = req->host[k];
     if (h.empty()) continue;
     DevBuf& d = pr.*kFieldBufs[k];
     HZ_TRY(d.ensure(h.size()));
-    HZ_CUDA(cudaMemcpy(d.ptr, h.data(), h.size(), cudaMemcpyHostToDevice));
-    std::vector<unsigned char>().swap(h);
+    HZ_CUDA(cudaMemcpyAsync(d.ptr, h.data(), h.size(), cudaMemcpyHostToDevice, pr.stream));
   }
+  HZ_CUDA(cudaStreamSynchronize(pr.stream));
+  for (auto& h : req->host) std::vector<unsigned char>().swap(h);
   if (req->flux_bytes) HZ_TRY(pr.mflux.ensure(req->flux_bytes));
-  HZ_CUDA(cudaStreamCreateWithFlags(&pr.stream, cudaStreamNonBlocking));
   return HZ_OK;
 }
 
