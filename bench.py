@@ -63,6 +63,9 @@ def parse():
                     help="sweep: only run --sweeps DD sweeps of the workload (for ncu captures); "
                          "batch: batched solves of the multi-problem workload; serve: served request stream")
     ap.add_argument("--batch", type=int, default=12, help="problems in --mode batch")
+    ap.add_argument("--batch-all", action="store_true",
+                    help="--mode batch: all 64 problems of the batched workload under a sweep budget")
+    ap.add_argument("--batch-sweeps", type=int, default=4, help="sweep budget per problem with --batch-all")
     ap.add_argument("--small-batch", type=int, default=32, help="small problems in --mode batch")
     ap.add_argument("--requests", type=int, default=40, help="arrivals in --mode serve")
     ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals per second in --mode serve")
@@ -83,7 +86,7 @@ def parse():
                     help="cfg2 is the benchmark workload; cfg1/cfg3 are reported separately; cfg3s is the "
                          "cfg3 physics and subdomain shape on a 256x256 mesh (for profiling)")
     ap.add_argument("--no-cfg3", action="store_true", help="skip the 1024^2 random-medium time-to-tolerance leg")
-    ap.add_argument("--cfg3-wh-cap", type=int, default=600, help="WaveHoltz iterations at most per subdomain")
+    ap.add_argument("--cfg3-wh-cap", type=int, default=300, help="WaveHoltz iterations at most per subdomain")
     ap.add_argument("--cfg3-wh-tol", type=float, default=1e-4, help="per-subdomain WaveHoltz tolerance")
     ap.add_argument("--cfg3-inner-tol", type=float, default=1e-1)
     ap.add_argument("--cfg3-restart", type=int, default=200)
@@ -969,6 +972,53 @@ def _batch_group(hz, cases, max_sweeps):
     return out
 
 
+def run_batch_all(args):
+    """--mode batch --batch-all: every problem of the 64-problem batched
+    workload (meshes 64^2..512^2, P 2..5, subdomains 4^2..32^2, N_t 30 to
+    16 000: five orders of magnitude of work) under a budget of
+    --batch-sweeps sweeps each, so the run is bounded by the largest problem's
+    sweeps rather than its convergence: one at a time, all concurrently
+    (hz_solve_batch, a stream per solve) and concurrently with the sweeps of
+    the packable ones issued as one packed launch per step.  FP32 sweeps
+    (20 WaveHoltz iterations), FP64 refinement; the kernel choice is the size
+    heuristic (autotuning times every variant, several sweeps each, which on
+    the largest problems would cost more than the budget).  Reports every
+    problem's status, sweeps, DOF-updates and N_t, and the throughput of each
+    schedule."""
+    import paper_2606_21695_gb300 as hz
+    from paper_2606_21695_gb300.api import Case
+    from workloads import configs
+
+    wls = configs.config4()
+    cases = [Case(w) for w in wls]
+    prs, ns = [c.pr for c in cases], [c.n for c in cases]
+    mk = lambda **kw: hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, max_sweeps=args.batch_sweeps,
+                                         autotune=0, **kw)
+    out = {"mode": "batch", "problems": len(cases), "sweep_budget": args.batch_sweeps}
+    t0 = time.perf_counter()
+    seq = [hz.hz_solve(c.pr, mk(pack=0), n=c.n) for c in cases]
+    out["sequential_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    st, sts, _, reps = hz.hz_solve_batch(prs, ns, mk(pack=0), 0, want_u=False)
+    out["concurrent_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pst, psts, _, preps = hz.hz_solve_batch(prs, ns, mk(pack=1), 0, want_u=False)
+    out["packed_s"] = time.perf_counter() - t0
+    dof = sum(r["dof_updates"] for r in reps)
+    out["dof_updates"] = dof
+    out["dof_updates_per_s"] = {"sequential": sum(s[2]["dof_updates"] for s in seq) / out["sequential_s"],
+                                "concurrent": dof / out["concurrent_s"],
+                                "packed": sum(r["dof_updates"] for r in preps) / out["packed_s"]}
+    out["packed_members"] = sum(r["sweep_variant"] == 4 for r in preps)
+    out["per_problem"] = [{"name": w.name, "nodes": c.n, "nt": r["nt"], "status": hz.STATUS_NAMES[s_],
+                           "sweeps": r["sweeps"], "rel_residual": r["rel_residual"], "kernel": r["sweep_variant"],
+                           "dof_updates": r["dof_updates"]}
+                          for w, c, r, s_ in zip(wls, cases, reps, sts)]
+    for c in cases:
+        c.close()
+    return out
+
+
 def run_batch(args):
     """--mode batch: the cheapest problems of the batched workload solved one
     at a time and together (hz_solve_batch); FP32 sweeps + FP64 refinement."""
@@ -976,6 +1026,9 @@ def run_batch(args):
 
     import paper_2606_21695_gb300 as hz
     from paper_2606_21695_gb300.api import Case
+
+    if args.batch_all:
+        return run_batch_all(args)
 
     wls = _cheap_cfg4(args.batch)
     cases = [Case(w) for w in wls]
