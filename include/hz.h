@@ -240,6 +240,9 @@ HZ_API hz_status hz_problem_nt(hz_problem pr, double cfl, int32_t* nt);
  * Returns HZ_ERR_NOT_CONVERGED (report filled, u_out written) if the budget
  * runs out, HZ_ERR_DIVERGED on non-finite values. */
 HZ_API hz_status hz_solve(hz_problem pr, const hz_solve_opts* opts, double* u_out, hz_solve_report* report);
+/* (With the environment variable HZ_SOLVE_LOG set, hz_solve and hz_solve_device print the
+ * residual after every refinement step, or the FGMRES residual estimate after every DD
+ * solve, to stderr: progress of long solves.) */
 /* Same with the solution written to device memory u_out_dev (n complex),
  * ordered on `stream` (a default stream -- legacy or per-thread -- is joined
  * by events and the work runs on the problem's own stream). */

@@ -1032,6 +1032,9 @@ hz_status fgmres_refine(Ctx& c, double* u, hz_status* result) {
       gvec[j] = cs[j] * gvec[j];
       k = j + 1;
       est = bnorm > 0.0 ? std::abs(gvec[j + 1]) / bnorm : 0.0;
+      if (std::getenv("HZ_SOLVE_LOG"))  // progress of long solves (diagnostics)
+        std::fprintf(stderr, "hz fgmres: DD solve %d, sweeps %d, residual estimate %.3e\n", c.rep.refinements,
+                     c.rep.sweeps, est);
       if (est <= 0.5 * o.tol || hnext == 0.0) break;
     }
     if (k == 0) {
@@ -1111,6 +1114,8 @@ hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report*
       return fail(HZ_ERR_DIVERGED, "refinement step increased the residual by orders of magnitude");
     }
     rep.rel_residual = rel;
+    if (std::getenv("HZ_SOLVE_LOG"))
+      std::fprintf(stderr, "hz refinement %d: sweeps %d, residual %.3e\n", rep.refinements, rep.sweeps, rel);
     if (rel <= o.tol) break;
     if (rep.refinements >= o.max_refine || rep.sweeps + 2 > o.max_sweeps) {  // a DD solve needs >= 2 sweeps
       result = fail(HZ_ERR_NOT_CONVERGED, "tolerance not reached within the refinement / sweep budget");
