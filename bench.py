@@ -403,8 +403,8 @@ def leg_cfg3(hz, args, stream):
     of its subdomains (its subdomain shape, element size, frequency and
     medium; 1.05 M nodes), FP32 sweeps + FP64 FGMRES refinement, CUDA events
     around the solve; its plain-FP64 time is the FP32 time scaled by the
-    measured FP64 / FP32 sweep-time ratio (labelled an estimate: ~40x
-    longer)."""
+    measured FP64 / FP32 sweep-time ratio (labelled an estimate: a plain-FP64
+    solve would take ~20x longer)."""
     import torch
 
     from paper_2606_21695_gb300.api import Case
