@@ -88,7 +88,7 @@ def parse():
     ap.add_argument("--no-cfg3", action="store_true", help="skip the 1024^2 random-medium time-to-tolerance leg")
     ap.add_argument("--cfg3-wh-cap", type=int, default=300, help="WaveHoltz iterations at most per subdomain")
     ap.add_argument("--cfg3-wh-tol", type=float, default=1e-4, help="per-subdomain WaveHoltz tolerance")
-    ap.add_argument("--cfg3-inner-tol", type=float, default=1e-1)
+    ap.add_argument("--cfg3-inner-tol", type=float, default=0.3)
     ap.add_argument("--cfg3-restart", type=int, default=200)
     ap.add_argument("--cfg3-max-sweeps", type=int, default=4000)
     ap.add_argument("--no-serve", action="store_true", help="skip the served-stream leg")
@@ -391,7 +391,7 @@ def cfg3_solve_opts(hz, args, max_sweeps=None):
     solves too inexact for any refinement to converge)."""
     return hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, inner_tol=args.cfg3_inner_tol,
                               wh_iters=args.cfg3_wh_cap, wh_tol=args.cfg3_wh_tol, gmres_restart=args.cfg3_restart,
-                              refine=hz.HZ_REFINE_FGMRES, refine_restart=30, max_refine=60,
+                              refine=hz.HZ_REFINE_FGMRES, refine_restart=60, max_refine=200,
                               max_sweeps=max_sweeps or args.cfg3_max_sweeps)
 
 
@@ -451,7 +451,7 @@ def leg_cfg3(hz, args, stream):
                               "rel_residual": rep["rel_residual"], "time_to_tol_s": tt, "sweeps": rep["sweeps"],
                               "dd_solves": rep["refinements"], "gmres_iters": rep["gmres_iters"], "nt": nt,
                               "wh_tol": opts.wh_tol, "wh_cap": opts.wh_iters, "wh_iters_max": rep["wh_iters_max"],
-                              "inner_tol": opts.inner_tol, "refinement": "FGMRES(30), FP64",
+                              "inner_tol": opts.inner_tol, "refinement": f"FGMRES({opts.refine_restart}), FP64",
                               "dof_updates": rep["dof_updates"], "dof_updates_per_s": rep["dof_updates"] / tt,
                               "sweep_kernel": rep["sweep_variant"], "fp64_over_fp32_sweep": r64 / r32,
                               "fp64_time_to_tol_s_estimated": tt * r64 / r32,
