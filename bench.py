@@ -480,12 +480,12 @@ def _serve_pool(k):
 
 
 def serve_opts(hz, precision):
-    """Options of a served request: FP64 flexible-GMRES refinement around DD
-    solves to 0.1 whose WaveHoltz runs per subdomain to a tolerance of 1e-4
-    (at most 600 iterations): the pool's high-frequency problems on wide
+    """Options of a served request: FP64 flexible-GMRES(60) refinement around
+    DD solves to 0.3 whose WaveHoltz runs per subdomain to a tolerance of 1e-4
+    (at most 300 iterations): the pool's high-frequency problems on wide
     subdomains stall with a fixed WaveHoltz count."""
-    return hz.hz_default_opts(precision=precision, tol=TOL, inner_tol=1e-1, wh_iters=600, wh_tol=1e-4,
-                              refine=hz.HZ_REFINE_FGMRES, refine_restart=30, max_refine=60, max_sweeps=6000)
+    return hz.hz_default_opts(precision=precision, tol=TOL, inner_tol=0.3, wh_iters=300, wh_tol=1e-4,
+                              refine=hz.HZ_REFINE_FGMRES, refine_restart=60, max_refine=200, max_sweeps=6000)
 
 
 def leg_serve(hz, n_requests, rate, pool_k, baseline_k, seed=5):
