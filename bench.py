@@ -74,10 +74,10 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--wh-iters", type=int, default=20, help="WaveHoltz iterations per sweep")
     ap.add_argument("--max-sweeps", type=int, default=5000)
-    ap.add_argument("--max-refine", type=int, default=20)
+    ap.add_argument("--max-refine", type=int, default=100)
     ap.add_argument("--refine", choices=["fgmres", "defect"], default="fgmres",
                     help="FP64 refinement: flexible GMRES with the DD solve as preconditioner, or defect correction")
-    ap.add_argument("--inner-tol", type=float, default=1e-1, help="relative tolerance of each DD solve")
+    ap.add_argument("--inner-tol", type=float, default=0.3, help="relative tolerance of each DD solve")
     ap.add_argument("--gs-passes", type=int, choices=[1, 2], default=1,
                     help="classical Gram-Schmidt passes per Arnoldi step")
     ap.add_argument("--robin", default="0,1", help="interface condition d_n + k (eta - i zeta): 'eta,zeta'")
@@ -625,7 +625,7 @@ def run_ours(args):
     opts = hz.hz_default_opts(precision=hz.HZ_FP32_REFINE, tol=TOL, inner_tol=args.inner_tol,
                               wh_iters=args.wh_iters, gmres_restart=60, max_sweeps=args.max_sweeps,
                               max_refine=args.max_refine, gs_passes=args.gs_passes, refine=refine,
-                              refine_restart=30)
+                              refine_restart=60)
     u = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
@@ -703,7 +703,7 @@ def run_ours(args):
             o64 = hz.hz_default_opts(precision=hz.HZ_FP64, tol=TOL, inner_tol=args.inner_tol,
                                      wh_iters=args.wh_iters, gmres_restart=60, max_sweeps=args.max_sweeps,
                                      max_refine=args.max_refine, gs_passes=args.gs_passes, refine=refine,
-                                     refine_restart=30)
+                                     refine_restart=60)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -784,7 +784,7 @@ def run_ours(args):
                        "omega": wl.omega, "nt": nt, "wh_iters": opts.wh_iters, "tol": TOL,
                        "outer": (f"GMRES(60) on the transmission data to {args.inner_tol:g}, {args.gs_passes} "
                                  f"classical Gram-Schmidt pass(es), inside FP64 "
-                                 + ("flexible GMRES(30) on K u = b" if args.refine == "fgmres"
+                                 + ("flexible GMRES(60) on K u = b" if args.refine == "fgmres"
                                     else "defect correction")),
                        "l2": "flushed (256 MB write) before each step",
                        "transmission": {"eta": robin[0], "zeta": robin[1]},
