@@ -324,7 +324,9 @@ HZ_API hz_status hz_sweep_rect(hz_problem pr, int32_t precision, int32_t nt, int
  * complex values, slot k at buf[k NE .. (k+1) NE - 1].  gather copies the
  * slots of lam into buf (the send buffer); scatter copies buf into the slots
  * of lam (after the receive).  The slot lists of a sender and its receiver
- * must enumerate the same interfaces in the same order. */
+ * must enumerate the same interfaces in the same order.  A slot outside the
+ * lambda vector (l not in 0..L-1 or e not in 0..3) is skipped: gather writes
+ * zeros for it, scatter writes nothing. */
 HZ_API hz_status hz_lambda_gather(hz_problem pr, const int32_t* slots, int32_t count, const double* lam, double* buf,
                                   void* stream);
 HZ_API hz_status hz_lambda_scatter(hz_problem pr, const int32_t* slots, int32_t count, const double* buf, double* lam,

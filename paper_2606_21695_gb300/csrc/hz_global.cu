@@ -544,22 +544,26 @@ hz_status launch_scale_inv_norm(const double* x, const double* norm2, double* y,
 }
 
 // One thread per complex entry of the listed slots; slot k occupies entries
-// [k NE, (k+1) NE) of the packed buffer.
-__global__ void lambda_slots_kernel(const int32_t* __restrict__ slots, int count, int NE, const double2* src,
+// [k NE, (k+1) NE) of the packed buffer.  A slot (l, e) outside the lambda
+// vector (l not in 0..L-1 or e not in 0..3) is skipped: gather writes zeros
+// for it, scatter writes nothing.
+__global__ void lambda_slots_kernel(const int32_t* __restrict__ slots, int count, int NE, int L, const double2* src,
                                     double2* dst, int gather) {
   const int64_t total = (int64_t)count * NE;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     const int k = (int)(q / NE), t = (int)(q % NE);
-    const int64_t slot = ((int64_t)slots[2 * k] * 4 + slots[2 * k + 1]) * NE + t;
-    if (gather) dst[q] = src[slot];
-    else dst[slot] = src[q];
+    const int l = slots[2 * k], e = slots[2 * k + 1];
+    const bool ok = l >= 0 && l < L && e >= 0 && e < 4;
+    const int64_t slot = ((int64_t)l * 4 + e) * NE + t;
+    if (gather) dst[q] = ok ? src[slot] : make_double2(0.0, 0.0);
+    else if (ok) dst[slot] = src[q];
   }
 }
 
-hz_status launch_lambda_slots(const int32_t* slots, int count, int NE, const double* src, double* dst, bool gather,
-                              cudaStream_t st) {
+hz_status launch_lambda_slots(const int32_t* slots, int count, int NE, int L, const double* src, double* dst,
+                              bool gather, cudaStream_t st) {
   const int64_t total = (int64_t)count * NE;
-  lambda_slots_kernel<<<grid_for(total, 256), 256, 0, st>>>(slots, count, NE, reinterpret_cast<const double2*>(src),
+  lambda_slots_kernel<<<grid_for(total, 256), 256, 0, st>>>(slots, count, NE, L, reinterpret_cast<const double2*>(src),
                                                              reinterpret_cast<double2*>(dst), gather ? 1 : 0);
   note_launch();
   HZ_CUDA(cudaGetLastError());

@@ -264,9 +264,9 @@ hz_status launch_scale_inv_norm(const double* x, const double* norm2, double* y,
                                 const int* flags_src = nullptr, int* flags_dst = nullptr);
 // Transmission-data slots (l, e) listed in slots (2 int32 per slot, device):
 // gather = true copies lam slot k (NE complex) to buf[k], else buf[k] to the
-// lam slot.
-hz_status launch_lambda_slots(const int32_t* slots, int count, int NE, const double* src, double* dst, bool gather,
-                              cudaStream_t st);
+// lam slot; slots outside the L x 4 slots of lam are skipped (gather: zeros).
+hz_status launch_lambda_slots(const int32_t* slots, int count, int NE, int L, const double* src, double* dst,
+                              bool gather, cudaStream_t st);
 // y = a*x + b*y
 hz_status launch_axpby(double a, const double* x, double b, double* y, int64_t n2, cudaStream_t st);
 

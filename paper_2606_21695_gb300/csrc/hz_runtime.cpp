@@ -1518,7 +1518,8 @@ hz_status hz_lambda_gather(hz_problem pr, const int32_t* slots, int32_t count, c
   if (count == 0) return HZ_OK;
   return guard([&]() -> hz_status {
     HZ_TRY(use_device(*pr));
-    return launch_lambda_slots(slots, count, pr->g.NE, lam, buf, /*gather=*/true, static_cast<cudaStream_t>(stream));
+    return launch_lambda_slots(slots, count, pr->g.NE, pr->g.L, lam, buf, /*gather=*/true,
+                               static_cast<cudaStream_t>(stream));
   });
 }
 
@@ -1528,7 +1529,8 @@ hz_status hz_lambda_scatter(hz_problem pr, const int32_t* slots, int32_t count, 
   if (count == 0) return HZ_OK;
   return guard([&]() -> hz_status {
     HZ_TRY(use_device(*pr));
-    return launch_lambda_slots(slots, count, pr->g.NE, buf, lam, /*gather=*/false, static_cast<cudaStream_t>(stream));
+    return launch_lambda_slots(slots, count, pr->g.NE, pr->g.L, buf, lam, /*gather=*/false,
+                               static_cast<cudaStream_t>(stream));
   });
 }
 

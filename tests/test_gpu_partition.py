@@ -102,3 +102,30 @@ def test_sweep_rect_rejects_rectangles_outside_the_grid(hz):
             assert e.value.status == hz.HZ_ERR_INVALID_ARG
     finally:
         case.close()
+
+
+def test_lambda_slots_outside_the_vector_are_skipped(hz):
+    import torch
+
+    from paper_2606_21695_gb300.api import Case
+
+    case = Case(configs.scaled(configs.config1(), 8, 8, 4, 4, name="slots_bad"))  # 2 x 2 subdomains
+    try:
+        nl = hz.hz_lambda_size(case.pr)
+        NE = nl // (4 * 4)
+        lam = torch.arange(2 * nl, dtype=torch.float64, device="cuda")
+        slots = _slots_dev([(1, 2), (4, 0), (-1, 1), (3, 4), (2, 3)])  # 2nd-4th are outside
+        buf = torch.full((2 * 5 * NE,), float("nan"), dtype=torch.float64, device="cuda")
+        hz.hz_lambda_gather(case.pr, slots, 5, lam, buf)
+        out = lam.clone()
+        hz.hz_lambda_scatter(case.pr, slots, 5, buf * 0 - 1, out)
+        torch.cuda.synchronize()
+        b = buf.view(5, NE, 2).cpu().numpy()
+        lv = lam.view(4, 4, NE, 2).cpu().numpy()
+        assert np.array_equal(b[0], lv[1, 2]) and np.array_equal(b[4], lv[2, 3])
+        assert not np.any(b[1:4])
+        o = out.view(4, 4, NE, 2).cpu().numpy()
+        changed = np.argwhere(np.any(o != lv, axis=(2, 3)))
+        assert sorted(map(tuple, changed)) == [(1, 2), (2, 3)]
+    finally:
+        case.close()
