@@ -969,6 +969,12 @@ hz_status fgmres_refine(Ctx& c, double* u, hz_status* result) {
     const double bnorm = std::sqrt(hb[1]);
     const double beta = std::sqrt(hb[0]);
     const double rel = bnorm > 0.0 ? beta / bnorm : 0.0;
+    // a cycle's update that multiplied the true residual (or made it
+    // non-finite: a singular least-squares system) diverged
+    if (!std::isfinite(rel) || (c.rep.refinements > 0 && !(rel < kResidualGrowth * c.rep.rel_residual))) {
+      c.rep.rel_residual = rel;
+      return fail(HZ_ERR_DIVERGED, "refinement cycle increased the residual by orders of magnitude");
+    }
     c.rep.rel_residual = rel;
     if (rel <= o.tol) {
       *result = HZ_OK;
@@ -1102,7 +1108,13 @@ hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report*
   int flags[4];
   hz_status result = HZ_OK;
   double bnorm = 0.0;
-  if (o.refine == HZ_REFINE_FGMRES) HZ_TRY(fgmres_refine(c, u, &result));
+  if (o.refine == HZ_REFINE_FGMRES) {
+    const hz_status fs = fgmres_refine(c, u, &result);
+    if (fs != HZ_OK) {
+      if (rep_out) *rep_out = rep;
+      return fs;
+    }
+  }
   while (o.refine != HZ_REFINE_FGMRES) {
     HZ_TRY(residual(pr, pr.bvec.as<double>(), u, pr.rvec.as<double>(), pr.small.as<double>(), st));
     HZ_TRY(fetch(c, 2, hb, flags));

@@ -248,21 +248,27 @@ hz_status hz_server_create(int32_t device, uint64_t hbm_budget_bytes, hz_server*
   HZ_CUDA(cudaGetDeviceCount(&ndev));
   if (device < 0 || device >= ndev) return fail(HZ_ERR_INVALID_ARG, "no such CUDA device");
   if (hbm_budget_bytes == 0) return fail(HZ_ERR_INVALID_ARG, "HBM budget must be > 0");
+  HZ_CUDA(cudaSetDevice(device));
+  std::unique_ptr<hz_server_s> s;
   try {
-    auto* s = new hz_server_s();
+    s = std::make_unique<hz_server_s>();
     s->device = device;
     s->budget = hbm_budget_bytes;
-    HZ_CUDA(cudaSetDevice(device));
     s->packer = std::make_unique<Packer>(device);
-    const char* env = std::getenv("HZ_SERVER_WORKERS");
-    int nw = env ? std::atoi(env) : 8;
-    nw = std::max(1, std::min(nw, 32));
-    for (int k = 0; k < nw; ++k) s->workers.emplace_back([s] { s->worker_loop(); });
-    *out = s;
-    return HZ_OK;
   } catch (...) {
-    return fail(HZ_ERR_INTERNAL, "could not start the server");
+    return fail(HZ_ERR_INTERNAL, "could not create the server");
   }
+  const char* env = std::getenv("HZ_SERVER_WORKERS");
+  int nw = env ? std::atoi(env) : 8;
+  nw = std::max(1, std::min(nw, 32));
+  try {
+    for (int k = 0; k < nw; ++k) s->workers.emplace_back([p = s.get()] { p->worker_loop(); });
+  } catch (...) {  // stop the workers that did start before the server goes away
+    hz_server_destroy(s.release());
+    return fail(HZ_ERR_INTERNAL, "could not start the server's worker threads");
+  }
+  *out = s.release();
+  return HZ_OK;
 }
 
 hz_status hz_server_submit(hz_server srv, hz_problem pr, const hz_solve_opts* opts, uint64_t* ticket) {

@@ -417,10 +417,12 @@ def test_solve_refinement_options_validated(hz):
     case.close()
 
 
-def test_time_step_beyond_cfl_reports_divergence(hz):
+@pytest.mark.parametrize("refine", ["defect", "fgmres"])
+def test_time_step_beyond_cfl_reports_divergence(hz, refine):
     wl = _wl(8, 8, 4, 4, 3, omega=2.0)
     case, pr = _pair(hz, wl)
-    opts = hz.hz_default_opts(nt_override=3, max_sweeps=20)
+    opts = hz.hz_default_opts(nt_override=3, max_sweeps=20,
+                              refine=hz.HZ_REFINE_FGMRES if refine == "fgmres" else hz.HZ_REFINE_DEFECT)
     with pytest.raises(hz.HzError) as e:
         hz.hz_solve(case.pr, opts, n=case.n)
     assert e.value.status == hz.HZ_ERR_DIVERGED
