@@ -45,7 +45,7 @@ UNIT = "DOF-updates/s"
 # DRAM bytes (read + write) of one launch of the one-warp-per-subdomain sweep
 # on the 256x256, P=3 workload, from one ncu capture of this kernel version
 # (coefficients and lambda read once; independent of the WaveHoltz count)
-SWEEP_WARP_TRAFFIC_BYTES = 7.66208e6
+SWEEP_WARP_TRAFFIC_BYTES = 7.608832e6
 TOL = 1e-8
 
 

@@ -81,6 +81,13 @@ __device__ __forceinline__ void warp_body(const WarpSweepArgs& x, int l, float4 
   float al0 = 0.f, alN = 0.f, b0r = 0.f, b0i = 0.f, bNr = 0.f, bNi = 0.f, g0 = 0.f, gN = 0.f;
 #pragma unroll
   for (int j = 0; j < NY; ++j) {
+    if (!SRC && j > 0 && j < NY - 1) {
+      // interior row without a source: only beta' differs from zero away from
+      // the edge columns, whose entries the lanes fill in parallel below
+      const double be = live ? (double)betaG[(int64_t)j * nlx + i] : 0.0;
+      bet[j] = (float)(be * wx_lane * x.wyr[j]);
+      continue;
+    }
     double be = 0.0, al = 0.0, br = 0.0, bi = 0.0, hm = 0.0;
     if (live) {
       const int64_t n = (int64_t)j * nlx + i;
@@ -115,6 +122,30 @@ __device__ __forceinline__ void warp_body(const WarpSweepArgs& x, int l, float4 
     if (j == NY - 1) { alN = (float)al; bNr = SRC ? 0.f : fbr; bNi = SRC ? 0.f : fbi; gN = gm; }
     if (j > 0 && j < NY - 1) {
       if (slot < 2) ec[j][slot] = make_float4((float)(al - 1.0), SRC ? 0.f : fbr, SRC ? 0.f : fbi, gm);
+    }
+  }
+  if (!SRC) {
+    // edge columns' interior rows, lane t taking row t of both: the same FP64
+    // expressions as the per-lane rows above (lambda and the boundary mass
+    // enter only on an interface edge), computed once per row rather than by
+    // the two edge lanes one row after another
+    for (int t = lane; t < NY - 1; t += 32) {
+      if (t == 0) continue;
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int cc = s == 0 ? 0 : nlx - 1;
+        const bool iface = s == 0 ? ifW : ifE;
+        const int64_t n = (int64_t)t * nlx + cc;
+        const double be = (double)betaG[n];
+        const double al = (double)alphaG[n];
+        double br = 0.0, bi = 0.0, hm = 0.0;
+        if (iface) {
+          br += a.wys[t] * lamL[2 * (s * a.NE + t)];
+          bi += a.wys[t] * lamL[2 * (s * a.NE + t) + 1];
+          hm += a.wys[t] * kedgeL[s * a.NE + t];
+        }
+        ec[t][s] = make_float4((float)(al - 1.0), (float)(be * br), (float)(be * bi), (float)(-be * a.eta * hm));
+      }
     }
   }
   __syncwarp();
@@ -266,19 +297,20 @@ __device__ __forceinline__ void warp_body(const WarpSweepArgs& x, int l, float4 
     put(2, t, mine, mine ? (double)vre[0] : 0.0, mine ? (double)vim[0] : 0.0);
     put(3, t, mine, mine ? (double)vre[NY - 1] : 0.0, mine ? (double)vim[NY - 1] : 0.0);
   }
-  // W / E edges: columns 0 and nlx-1 hold every row
-  if (lane == 0 || lane == nlx - 1) {
+  // W / E edges: columns 0 and nlx-1 hold every row.  They are staged in the
+  // edge table (not read after the time loop) so that lane t writes row t of
+  // both edges, instead of two lanes running the FP64 update row by row.
+  if (slot < 2) {
 #pragma unroll
-    for (int j = 0; j < NY; ++j) {
-      if (lane == 0) put(0, j, true, (double)vre[j], (double)vim[j]);
-      if (lane == nlx - 1) put(1, j, true, (double)vre[j], (double)vim[j]);
-    }
+    for (int j = 0; j < NY; ++j) ec[j][slot] = make_float4(vre[j], vim[j], 0.f, 0.f);
   }
-  if (lane == 0) {
-    for (int t = NY; t < NE; ++t) {
-      put(0, t, false, 0.0, 0.0);
-      put(1, t, false, 0.0, 0.0);
-    }
+  __syncwarp();
+  for (int t = lane; t < NE; t += 32) {
+    const bool has = t < NY;
+    const float4 uw = has ? ec[t][0] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 ue = has ? ec[t][1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    put(0, t, has, (double)uw.x, (double)uw.y);
+    put(1, t, has, (double)ue.x, (double)ue.y);
   }
 }
 
