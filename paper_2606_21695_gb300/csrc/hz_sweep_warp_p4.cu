@@ -1,41 +1,10 @@
 // Register-resident sweep instantiations for degree 4: one warp per
 // subdomain (h = 1) and, for the larger shapes, h = 2 or 4 warps per
 // subdomain (row bands).
-#include "hz_sweep_band.cuh"
-#include "hz_sweep_warp.cuh"
+#include "hz_sweep_warp_launch.cuh"
 
 namespace hz {
 namespace warp_sweep {
-namespace {
-template <int P, int SY, int H>
-hz_status launch(const WarpSweepArgs& a, cudaStream_t st) {
-  if constexpr (H == 1) {
-    const int blocks = a.L;  // one subdomain (one warp) per block
-    const bool rm = a.base.eta != 0.0;  // interface boundary mass present
-    if (a.base.u0) {  // warm start (the boundary-mass terms kept: zero when eta = 0)
-      if (a.base.rhs) sweep_warp_kernel<P, SY, true, true, true><<<blocks, 32, 0, st>>>(a);
-      else sweep_warp_kernel<P, SY, false, true, true><<<blocks, 32, 0, st>>>(a);
-    } else if (a.base.rhs) {
-      if (rm) sweep_warp_kernel<P, SY, true, true><<<blocks, 32, 0, st>>>(a);
-      else sweep_warp_kernel<P, SY, true, false><<<blocks, 32, 0, st>>>(a);
-    } else {
-      if (rm) sweep_warp_kernel<P, SY, false, true><<<blocks, 32, 0, st>>>(a);
-      else sweep_warp_kernel<P, SY, false, false><<<blocks, 32, 0, st>>>(a);
-    }
-  } else {
-    const int blocks = a.L;  // one subdomain (H warps) per block
-    if (a.base.u0) {
-      if (a.base.rhs) band_sweep::sweep_band_kernel<P, SY, true, H, true><<<blocks, H * 32, 0, st>>>(a);
-      else band_sweep::sweep_band_kernel<P, SY, false, H, true><<<blocks, H * 32, 0, st>>>(a);
-    } else if (a.base.rhs) band_sweep::sweep_band_kernel<P, SY, true, H><<<blocks, H * 32, 0, st>>>(a);
-    else band_sweep::sweep_band_kernel<P, SY, false, H><<<blocks, H * 32, 0, st>>>(a);
-  }
-  note_launch();
-  HZ_CUDA(cudaGetLastError());
-  return HZ_OK;
-}
-}  // namespace
-
 hz_status launch_p4(int sy, int h, const WarpSweepArgs& a, cudaStream_t st) {
   switch (sy) {
     case 1: if (h == 1) return launch<4, 1, 1>(a, st); return HZ_ERR_UNSUPPORTED;
