@@ -19,8 +19,9 @@ Plain, slow, obviously-correct NumPy/SciPy restatement of the paper
                (lambda-iteration), sign read as -2ik), plain and GMRES outer
                iterations (Sec. 3, Krylov acceleration), the global operator,
                residual, direct solve and FP64 refinement (Sec. 7, DD as a
-               preconditioner).
-* ``krylov``-- a plain restarted GMRES (minimal-residual definition).
+               preconditioner: defect correction or flexible GMRES).
+* ``krylov``-- plain restarted GMRES and flexible GMRES (minimal-residual
+               definitions, least squares on the Hessenberg matrix).
 
 Parity status of each function is listed in its docstring.  The WaveHoltz
 and outer-iteration *convergence rates* are "parity unpinned": they are

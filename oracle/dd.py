@@ -422,10 +422,35 @@ class Problem:
                                         "wh_iters": wh_total}
 
     def solve(self, Nt=None, m_wh=5, wh_tol=0.0, tol=1e-8, outer="gmres", restart=50, inner_tol=1e-10,
-              max_sweeps=500, max_refine=10, inner="waveholtz"):
-        """FP64 defect correction around the DD solve (Sec. 7: the DDM acts as
-        a preconditioner): u_{k+1} = u_k + DD(b - K u_k) until
-        ||b - K u|| <= tol ||b||.  Returns (u, info)."""
+              max_sweeps=500, max_refine=10, inner="waveholtz", refine="defect", refine_restart=30):
+        """FP64 refinement around the DD solve (Sec. 7: the DDM acts as a
+        preconditioner) until ||b - K u|| <= tol ||b||.
+
+        refine="defect": u_{k+1} = u_k + DD(b - K u_k).
+        refine="fgmres": flexible GMRES(refine_restart) on K u = b with the DD
+        solve of each basis vector as the right preconditioner
+        (krylov.fgmres; the DD solve stops at a tolerance and, with a fixed
+        WaveHoltz count, is only real-linear, so it is a different map at
+        every step).  max_refine bounds the DD solves in both.
+        Returns (u, info)."""
+        if refine == "fgmres":
+            Nt = self.choose_nt() if Nt is None else Nt
+            b = self.rhs()
+            shape = b.shape
+            sweeps = [0]
+
+            def precond(v):
+                e, info = self.dd_solve(v.reshape(shape), Nt, m_wh, wh_tol, outer, restart, inner_tol, max_sweeps,
+                                        inner)
+                sweeps[0] += info["sweeps"]
+                return e.ravel()
+
+            u, info = krylov.fgmres(lambda x: self.apply_K(x.reshape(shape)).ravel(), precond, b.ravel(),
+                                    restart=refine_restart, tol=tol, maxit=max_refine)
+            return u.reshape(shape), {"rel_residual": info["hist"][-1], "hist": info["hist"], "est": info["est"],
+                       "sweeps": sweeps[0], "refinements": info["precond"]}
+        if refine != "defect":
+            raise ValueError(refine)
         b = self.rhs()
         bn = np.linalg.norm(b)
         u = np.zeros_like(b)

@@ -224,6 +224,19 @@ def test_dd_with_waveholtz_inner_and_refinement_reaches_direct_solution():
     assert np.linalg.norm(u - ud) / np.linalg.norm(ud) < 1e-8
 
 
+def test_fgmres_refinement_reaches_direct_solution():
+    """Flexible GMRES around inexact DD solves (5 WaveHoltz iterations, DD
+    solves stopped at 1e-2): the same global solution as the direct solve."""
+    pr = _problem(8, 8, 4, 4, 3, omega=10.0, seed=2)
+    ud = pr.direct_solve()
+    u, info = pr.solve(m_wh=5, tol=1e-11, inner_tol=1e-2, restart=60, max_refine=40, refine="fgmres",
+                       refine_restart=20)
+    assert info["rel_residual"] <= 1e-11, info["hist"]
+    assert np.linalg.norm(pr.residual(u)) <= 1.0001e-11 * np.linalg.norm(pr.rhs())
+    assert np.linalg.norm(u - ud) / np.linalg.norm(ud) < 1e-8
+    assert info["refinements"] <= 40 and info["sweeps"] > 0
+
+
 def test_real_gmres_reaches_inexact_fixed_point():
     """With a fixed WaveHoltz count the DD map is real-linear; real GMRES on
     the interleaved vector converges to its fixed point (checked against the
