@@ -234,11 +234,15 @@ HZ_API void hz_problem_destroy(hz_problem pr);
 HZ_API hz_status hz_problem_nt(hz_problem pr, double cfl, int32_t* nt);
 
 /* ------------------------------------------------------------------ solve --
- * Full solve to opts->tol: FP64 defect correction u <- u + DD(b - K u), each
- * DD step an outer iteration on lambda whose matvec is one sweep (one kernel
- * launch over all subdomains).  u_out: host buffer of n complex values.
+ * Full solve to opts->tol: FP64 refinement on the global residual (Sec. 7),
+ * either defect correction u <- u + DD(b - K u) or flexible GMRES on K u = b
+ * with the DD solve as right preconditioner (opts->refine); each DD solve is
+ * an outer iteration on lambda whose matvec is one sweep (one kernel launch
+ * over all subdomains).  u_out: host buffer of n complex values.
  * Returns HZ_ERR_NOT_CONVERGED (report filled, u_out written) if the budget
- * runs out, HZ_ERR_DIVERGED on non-finite values. */
+ * runs out; HZ_ERR_DIVERGED (report filled) on non-finite values, a Krylov
+ * operator norm beyond 1e8, or a refinement step or FGMRES cycle that
+ * multiplied the residual by 1e4 or more. */
 HZ_API hz_status hz_solve(hz_problem pr, const hz_solve_opts* opts, double* u_out, hz_solve_report* report);
 /* (With the environment variable HZ_SOLVE_LOG set, hz_solve and hz_solve_device print the
  * residual after every refinement step, or the FGMRES residual estimate after every DD

@@ -1139,7 +1139,10 @@ hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report*
     if (o.wh_adaptive) oi.wh_tol = std::min(1e-2, std::max(o.wh_tol > 0.0 ? o.wh_tol : 1e-6, 0.1 * rel));
     Ctx ci{pr, oi, nt, st, rep, c.n2};
     hz_status s = dd_solve(ci, pr.rvec.as<double>(), u);
-    if (s != HZ_OK && s != HZ_ERR_NOT_CONVERGED) return s;
+    if (s != HZ_OK && s != HZ_ERR_NOT_CONVERGED) {
+      if (rep_out) *rep_out = rep;
+      return s;
+    }
     rep.refinements++;
   }
   HZ_CUDA(cudaMemcpyAsync(flags, pr.flags.ptr, 16, cudaMemcpyDeviceToHost, st));
