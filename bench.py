@@ -574,7 +574,7 @@ def leg_cpu(args, cfg1_handle, t_start, cfg2_dof_per_solve, cfg3):
     on a piece of the 1024^2 workload (all cores), its own cfg1 solve to 1e-8
     (one core, run beside the GPU legs), and time-to-tolerance estimates for
     the two big workloads (the GPU solve's DOF-updates / the oracle's rate)."""
-    pool = OraclePool("cfg2", m_wh=5)
+    pool = OraclePool(args.workload, m_wh=args.wh_iters)
     s2 = pool.sample(args.cpu_sample_s)
     pool.close()
     out = {"value": s2["value"], "unit": UNIT, "cores": s2["cores"], "kind": "oracle", "sample": s2["sample"],
@@ -596,6 +596,20 @@ def leg_cpu(args, cfg1_handle, t_start, cfg2_dof_per_solve, cfg3):
 
 
 # ------------------------------------------------------------ our arm ----
+def step_config(wl, nt, args, world):
+    """The timed step's workload, the same in both arms' JSON lines."""
+    robin = [float(v) for v in args.robin.split(",")]
+    return {"workload": wl.name, "mesh": f"{wl.nx}x{wl.ny} quads", "degree": wl.P,
+            "subdomains": f"{wl.nx // wl.sub_nx}x{wl.ny // wl.sub_ny} of {wl.sub_nx}x{wl.sub_ny}",
+            "omega": wl.omega, "nt": nt, "wh_iters": args.wh_iters, "tol": TOL,
+            "outer": (f"GMRES(60) on the transmission data to {args.inner_tol:g}, {args.gs_passes} "
+                      f"classical Gram-Schmidt pass(es), inside FP64 "
+                      + ("flexible GMRES(60) on K u = b" if args.refine == "fgmres" else "defect correction")),
+            "l2": "flushed (256 MB write) before each step",
+            "transmission": {"eta": robin[0], "zeta": robin[1]},
+            "parallelism": f"{world} independent solves (one per GPU)"}
+
+
 def run_ours(args):
     t_start = time.perf_counter()
     rank, world, local = dist_env()
@@ -779,16 +793,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (subdomain WaveHoltz) + f64 (outer, residual)",
             "data": "synthetic (seeded generators)",
-            "config": {"workload": wl.name, "mesh": f"{wl.nx}x{wl.ny} quads", "degree": P,
-                       "subdomains": f"{wl.nx // wl.sub_nx}x{wl.ny // wl.sub_ny} of {wl.sub_nx}x{wl.sub_ny}",
-                       "omega": wl.omega, "nt": nt, "wh_iters": opts.wh_iters, "tol": TOL,
-                       "outer": (f"GMRES(60) on the transmission data to {args.inner_tol:g}, {args.gs_passes} "
-                                 f"classical Gram-Schmidt pass(es), inside FP64 "
-                                 + ("flexible GMRES(60) on K u = b" if args.refine == "fgmres"
-                                    else "defect correction")),
-                       "l2": "flushed (256 MB write) before each step",
-                       "transmission": {"eta": robin[0], "zeta": robin[1]},
-                       "parallelism": f"{world} independent solves (one per GPU)"},
+            "config": step_config(wl, nt, args, world),
             "time_to_tol_s": {"fp32_refine": elapsed / args.steps, "fp64": fp64["seconds"] if fp64 else None,
                               "cfg3_piece_fp32_refine": cfg3["piece_solve"]["time_to_tol_s"] if cfg3 else None,
                               "cfg3_piece_fp64_estimated": (cfg3["piece_solve"]["fp64_time_to_tol_s_estimated"]
@@ -841,8 +846,8 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return None
-    wl = workload("cfg2")
-    pool = OraclePool("cfg2", m_wh=5)
+    wl = workload(args.workload)
+    pool = OraclePool(args.workload, m_wh=args.wh_iters)
     vals = []
     desc, cores = "", pool.cores
     try:
@@ -860,7 +865,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded generators)",
-        "config": {"workload": wl.name, "sample": desc},
+        "config": step_config(wl, pool.info["nt"], args, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
