@@ -123,7 +123,8 @@ typedef struct {
   int32_t max_sweeps;    /* budget of DD sweeps over the whole solve */
   int32_t outer;         /* hz_outer */
   int32_t gmres_restart; /* GMRES restart length m */
-  int32_t wh_iters;      /* WaveHoltz iterations per sweep (maximum if wh_tol > 0) */
+  int32_t wh_iters;      /* WaveHoltz iterations per sweep (maximum if wh_tol > 0; 0 with
+                            wh_tol > 0: at most 1000) */
   double wh_tol;         /* > 0: a subdomain stops when ||u^{m+1}-u^m|| <= wh_tol ||u^{m+1}|| */
   int32_t nt_override;   /* > 0: time steps per period; 0: from the CFL rule */
   double cfl;            /* dt = cfl * 2 / (c_max sqrt(lx + ly)) */

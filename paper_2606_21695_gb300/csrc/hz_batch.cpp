@@ -34,7 +34,7 @@ extern "C" hz_status hz_solve_batch(const hz_problem* problems, int32_t count, c
   if (!problems || count < 0 || !statuses) return fail(HZ_ERR_INVALID_ARG, "null argument or negative count");
   if (count == 0) return HZ_OK;
   hz_solve_opts o;
-  if (opts) o = *opts;
+  if (opts) o = effective_opts(*opts);
   else hz_default_opts(&o);
   for (int k = 0; k < count; ++k) {
     if (!problems[k]) return fail(HZ_ERR_INVALID_ARG, "null problem in batch");

@@ -93,6 +93,10 @@ hz_status residual(Problem& pr, const double* b, const double* u, double* r, dou
 hz_status rhs(Problem& pr, double* b, cudaStream_t st);
 hz_status assemble_add(Problem& pr, const double* u_sub, double* u, cudaStream_t st);
 hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report* rep, cudaStream_t st);
+// The options a solve runs with: wh_iters = 0 together with a WaveHoltz
+// tolerance stands for the default cap of kDefaultWhCap iterations.
+constexpr int kDefaultWhCap = 1000;
+hz_solve_opts effective_opts(const hz_solve_opts& o);
 hz_status check_ready(const Problem& pr);
 // Geometry of a mapped mesh from 2n node coordinates (x, y interleaved):
 // validates J > 0 at every GLL node and uploads the metric and weights.

@@ -1067,8 +1067,15 @@ hz_status fgmres_refine(Ctx& c, double* u, hz_status* result) {
 
 }  // namespace
 
-hz_status solve(Problem& pr, const hz_solve_opts& o, double* u, hz_solve_report* rep_out, cudaStream_t st) {
+hz_solve_opts effective_opts(const hz_solve_opts& o) {
+  hz_solve_opts e = o;
+  if (e.wh_iters == 0 && e.wh_tol > 0.0) e.wh_iters = kDefaultWhCap;
+  return e;
+}
+
+hz_status solve(Problem& pr, const hz_solve_opts& o_in, double* u, hz_solve_report* rep_out, cudaStream_t st) {
   const auto t0 = std::chrono::steady_clock::now();
+  const hz_solve_opts o = effective_opts(o_in);
   HZ_TRY(check_ready(pr));
   if (!(o.tol >= 0.0) || o.max_sweeps < 1 || o.gmres_restart < 1 || o.gmres_restart > 1000 || o.wh_iters < 1 ||
       !(o.cfl > 0.0) || o.max_refine < 0 || !(o.inner_tol >= 0.0) || !(o.wh_tol >= 0.0))
