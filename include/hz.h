@@ -14,11 +14,13 @@
  *     the sign of the 2ik term is read as minus, which makes the DD fixed
  *     point equal to the global discrete solution)
  *   - each subdomain solved by WaveHoltz (Sec. 5, eq. (WaveHoltz), modified
- *     leapfrog), one CUDA thread block per subdomain, all subdomains in one
- *     launch (Sec. 6, Algorithm 1)
+ *     leapfrog), all subdomains in one launch per DD sweep (Sec. 6,
+ *     Algorithm 1): one warp, a few warps, one block or one thread-block
+ *     cluster per subdomain, by subdomain size
  *   - outer iteration: GMRES on the transmission data (Sec. 3, Krylov
- *     acceleration) inside FP64 defect correction on the global residual
- *     (Sec. 7: the DD cycle is a preconditioner and may run in lower precision).
+ *     acceleration) inside FP64 refinement on the global residual, defect
+ *     correction or flexible GMRES (Sec. 7: the DD cycle is a preconditioner
+ *     and may run in lower precision).
  *
  * Conventions for every function below:
  *   - Return value: HZ_OK or an error code; hz_last_error() gives the message
