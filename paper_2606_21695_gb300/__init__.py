@@ -1,5 +1,5 @@
 """GB300-native domain-decomposition Helmholtz solver (WaveHoltz subdomain
-solves, one CUDA thread block per subdomain).
+solves, every subdomain of a sweep in one CUDA kernel launch).
 
 The compute path is the CUDA library ``_lib/libhz.so`` (C ABI in
 ``include/hz.h``); this package is its ctypes binding.  Importing it loads

@@ -112,3 +112,24 @@ def test_noalloc_residual_limits_are_checked_on_the_host(hz):
         assert _status(e) == hz.HZ_ERR_UNSUPPORTED and "node rows" in str(e.value)
     finally:
         hz.hz_mesh_destroy(m)
+
+
+def test_options_struct_layout_matches_the_library(hz):
+    """hz_default_opts (host only) fills the binding's struct with the
+    documented defaults, last field included, and writes nothing past it."""
+    class Guarded(C.Structure):
+        _fields_ = [("opts", hz.hz_solve_opts), ("guard", C.c_uint8 * 64)]
+
+    g = Guarded()
+    C.memset(C.addressof(g.guard), 0xA5, 64)
+    hz.load().hz_default_opts(C.byref(g.opts))
+    assert bytes(g.guard) == b"\xa5" * 64
+    o = g.opts
+    assert (o.precision, o.tol, o.max_sweeps, o.outer, o.gmres_restart, o.wh_iters) == \
+           (hz.HZ_FP64, 1e-8, 2000, hz.HZ_OUTER_GMRES, 60, 20)
+    assert (o.wh_tol, o.nt_override, o.cfl, o.inner_tol, o.max_refine) == (0.0, 0, 0.9, 1e-2, 20)
+    assert (o.autotune, o.wh_adaptive, o.pack, o.graphs, o.gs_passes, o.wh_warm) == (1, 0, 1, 1, 1, 0)
+    assert (o.refine, o.refine_restart) == (hz.HZ_REFINE_DEFECT, 30)
+    # the binding's keyword form sets fields by name over the same defaults
+    k = hz.hz_default_opts(refine=hz.HZ_REFINE_FGMRES, refine_restart=60, tol=1e-9)
+    assert (k.refine, k.refine_restart, k.tol, k.gmres_restart) == (hz.HZ_REFINE_FGMRES, 60, 1e-9, 60)
