@@ -1,7 +1,9 @@
 // Warp-per-subdomain DD sweep (FP32), for subdomains of at most 32 node
 // columns and NY = SY*P+1 rows: lane i owns node column i, every row of it
-// in registers for the whole WaveHoltz loop (p, p-dot, v, alpha, beta,
-// beta*b).  The time step needs no shared memory and no barrier:
+// in registers for the whole WaveHoltz loop (p, p-dot, v, beta'; alpha and
+// beta*b only where they differ from 1 and 0: rows 0 and NY-1 in registers,
+// the edge columns' other rows in a small shared table that the two edge
+// lanes read).  The time step needs no barrier:
 //   x part of A p: assembled 1D row, own-element neighbours gathered by P
 //                  indexed shuffles plus one hand-off for the element to the
 //                  left (hz_sweep_xrow.cuh), per-lane coefficients in registers;
@@ -10,7 +12,8 @@
 //                  class (hz_gll_const.h), constant-bank operands of the FMAs.
 // Same arithmetic as the block sweep (Algorithm 1, modified leapfrog and
 // eq. (WaveHoltz) with the -1/(i omega) sign and 2/N_t scaling; lambda
-// update -lambda - 2ik u); several subdomains per block, one per warp.
+// update -lambda - 2ik u); one subdomain per one-warp block, or per item of
+// the persistent packed launch (hz_sweep_packed.cu).
 #pragma once
 
 #include <cuda_runtime.h>
