@@ -1,8 +1,11 @@
 // FP64 kernels around the sweep: leapfrog coefficients, right-hand side,
 // global operator residual, assembly of subdomain copies, and the vector
-// operations of the outer Krylov iteration.  All are HBM-bound streaming
-// kernels with coalesced x-fastest access; reductions are two-pass with a
-// fixed summation order (deterministic results).
+// operations of the outer Krylov iteration.  All stream their data once with
+// coalesced x-fastest access.  The right-hand side and the assembly are
+// HBM-bound; the residual and the Krylov vector kernels do enough FP64
+// arithmetic per byte that this part's FP64 pipe bounds them, so they are
+// written with the fewest FP64 operations (FMA chains).  Reductions are
+// two-pass with a fixed summation order (deterministic results).
 #include <cuda_runtime.h>
 
 #include <atomic>
