@@ -1,7 +1,8 @@
 // Host runtime behind the C ABI: problem state, coefficient preparation,
-// the outer iteration on the transmission data (GMRES / plain / real GMRES,
-// Sec. 3), FP64 defect correction on the global residual (Sec. 7), and the
-// extern "C" entry points declared in include/hz.h.
+// the sweep kernel choice and its autotuner, the outer iteration on the
+// transmission data (GMRES / plain / real GMRES, Sec. 3), the FP64
+// refinement on the global residual (defect correction or flexible GMRES,
+// Sec. 7), and the extern "C" entry points declared in include/hz.h.
 #include <cuda_runtime.h>
 
 #include <algorithm>
