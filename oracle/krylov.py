@@ -21,7 +21,10 @@ problem: such an M_j is not one fixed linear map).  After k steps of a cycle
 x = x_start + Z_k y, y minimising || r_start - A Z_k y ||_2; the Arnoldi
 relation A Z_k = V_{k+1} H_k gives that as the small least-squares problem
 || beta e1 - H_k y ||.  With M_j = I it is GMRES; with one fixed linear M it is
-GMRES on A M followed by x = M y (right preconditioning).
+GMRES on A M followed by x = M y (right preconditioning).  Both special cases,
+the least-squares definition over the preconditioner's own outputs, the
+one-step solve with the exact inverse and the restarts are pinned in
+tests/test_oracle_krylov.py.
 """
 
 from __future__ import annotations
