@@ -25,6 +25,7 @@
 #include <thread>
 #include <vector>
 
+#include "hz_admission.h"
 #include "hz_internal.h"
 #include "hz_pack.h"
 #include "hz_problem.h"
@@ -155,20 +156,8 @@ struct hz_server_s {
   clk::time_point t_start = clk::now();
 
   // First queued request that fits in the budget (removed from the queue), or
-  // null.  Requests ahead of it that do not fit count one more pass-over; one
-  // that reached kMaxPassOver stops the scan, so it is admitted next.
-  Request* pick() {
-    for (auto it = queue.begin(); it != queue.end(); ++it) {
-      Request* r = *it;
-      if (in_use + r->bytes <= budget) {
-        for (auto jt = queue.begin(); jt != it; ++jt) (*jt)->passed_over++;
-        queue.erase(it);
-        return r;
-      }
-      if (r->passed_over >= kMaxPassOver) return nullptr;
-    }
-    return nullptr;
-  }
+  // null (hz_admission.h).
+  Request* pick() { return first_fit(queue, in_use, budget, kMaxPassOver); }
 
   void worker_loop() {
     cudaSetDevice(device);
